@@ -1,0 +1,210 @@
+/*
+ * mci.h -- C ABI of the GB300-native FFT multichannel interpolation library.
+ *
+ * Method: Cheng & Kou, "FFT multichannel interpolation and application to
+ * image super-resolution".  A periodic signal f on [0, 2 pi) is observed
+ * through M linear systems with Fourier multipliers b_m(n) (Section 3,
+ * Eq. (sysfunction)); each response g_m is sampled P times at t_p = 2 pi p / P
+ * (the paper calls P "L").  The library reconstructs f -- or its circular
+ * Hilbert transform, or its derivative -- on the grid t_j = 2 pi j / T from
+ * those M*P samples, assuming f is bandlimited to the band
+ * {N1, ..., N1 + M*P - 1} (Eq. (bandsignal)), or approximating it there when it
+ * is not (operator T_N, Eq. (appxi operator)).  The computation follows the
+ * FFT form of Theorem (MCIeq), Eq. (DFTexpression): an FFT of every channel,
+ * a per-residue solve with the inverse of the M x M system matrix H_n of
+ * Eq. (defH) (Eq. (matrixeqn1)), and an inverse FFT that evaluates the
+ * result.  Images are processed separably, rows then columns (Section 5.2).
+ *
+ * Conventions shared by every entry point:
+ *   - All sample and pixel buffers are DEVICE pointers owned by the caller.
+ *     The library never frees them and never keeps them past a call.
+ *   - Streams are cudaStream_t values passed as void*; NULL is the legacy
+ *     default stream.  Every call except mci_plan, mci_plan_info and
+ *     mci_destroy is asynchronous and stream-ordered: it only enqueues work.
+ *   - Errors are returned as mci_status.  A call that returns an error has
+ *     enqueued nothing.  Errors that only the device can see (a size class
+ *     index out of range, an image size the plan does not hold) make the
+ *     kernels skip the affected signal or image and set a device status word
+ *     that mci_plan_info reports.
+ *   - No call allocates device memory except mci_plan (tables and workspace).
+ *   - The result of a real-sample reconstruction is the real part of the
+ *     band-limited interpolant, as in the experiments of Section 5.1.
+ */
+#ifndef MCI_H
+#define MCI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mci_plan_s* mci_plan_t;   /* opaque; owned by the library */
+typedef void* mci_stream_t;              /* a cudaStream_t */
+
+typedef enum {
+    MCI_OK = 0,
+    MCI_ERR_INVALID_ARG = -1,      /* null pointer, bad enum, inconsistent sizes */
+    MCI_ERR_UNSUPPORTED_SIZE = -2, /* P, T or a buffer the kernels cannot take */
+    MCI_ERR_SINGULAR = -3,         /* a system matrix is singular under MCI_SINGULAR_ERROR */
+    MCI_ERR_CUDA = -4,             /* a CUDA runtime call failed */
+    MCI_ERR_OOM = -5,              /* device allocation failed in mci_plan */
+    MCI_ERR_TIMEOUT = -6,          /* a device-side bounded wait gave up */
+    MCI_ERR_DEVICE = -7            /* a device-side check failed (see mci_plan_info) */
+} mci_status;
+
+/* Linear systems (the paper's h_m / b_m(n), Eq. (sysfunction)). */
+enum {
+    MCI_SYS_IDENTITY = 0, /* b(n) = 1                                   */
+    MCI_SYS_DERIV = 1,    /* b(n) = (i n)^order, order >= 1 (Example 2)  */
+    MCI_SYS_HILBERT = 2,  /* b(n) = -i sgn(n) (Examples 3, 5)            */
+    MCI_SYS_SHIFT = 3,    /* b(n) = e^{i n tau}                          */
+    MCI_SYS_CUSTOM = 4    /* b(n) from a host table, see mci_system      */
+};
+
+typedef struct {
+    int kind;             /* MCI_SYS_*                                                   */
+    int order;            /* MCI_SYS_DERIV: derivative order (1 or more)                 */
+    double tau;           /* MCI_SYS_SHIFT: shift                                        */
+    const double* custom; /* MCI_SYS_CUSTOM: host table read during mci_plan only: for
+                             each size class c in order, 2*M*P_c doubles (re, im) of b(n)
+                             for n = N1_c .. N1_c + M*P_c - 1                            */
+} mci_system;
+
+/* Output operators applied to the reconstruction (Example 6, and the remark
+ * closing Section 3 on reconstructing Q(f)).  OR-able; outputs are stored in
+ * the order F, HILBERT, DERIV. */
+enum {
+    MCI_OUT_F = 1,       /* f itself                       */
+    MCI_OUT_HILBERT = 2, /* circular Hilbert transform of f (Section 2) */
+    MCI_OUT_DERIV = 4    /* f'                             */
+};
+
+enum { MCI_FP32 = 0, MCI_FP64 = 1 };
+
+/* What to do where H_n is singular (Remark (aequal0)). */
+enum {
+    MCI_SINGULAR_PINV = 0,  /* Moore-Penrose pseudo-inverse: minimum-norm solution of
+                               A_n H_n = D_n (Eq. (matrixeqn1)); default            */
+    MCI_SINGULAR_ERROR = 1, /* mci_plan fails with MCI_ERR_SINGULAR                  */
+    MCI_SINGULAR_ZERO = 2   /* q_{mk}(n) = 0 at that residue, as Remark (aequal0)     */
+};
+
+/* Where the channels come from. */
+enum {
+    MCI_CHANNELS_MEASURED = 0, /* the caller passes all M channels' samples            */
+    MCI_CHANNELS_FD = 1        /* the caller passes one channel (system 0, which must be
+                                  the identity); the others are its three-point centred
+                                  differences (Section 5.2): first derivative
+                                  (x[p+1] - x[p-1]) / (2h), second derivative
+                                  (x[p+1] - 2x[p] + x[p-1]) / h^2, h = 2 pi / P, periodic.
+                                  Only MCI_SYS_IDENTITY and MCI_SYS_DERIV (order 1, 2). */
+};
+
+#define MCI_MAX_CHANNELS 8
+#define MCI_MAX_SIZES 32
+
+typedef struct {
+    int M;                   /* channels, 1 .. MCI_MAX_CHANNELS                            */
+    const mci_system* sys;   /* M systems (host, read during mci_plan only)                */
+    int n_sizes;             /* size classes, 1 .. MCI_MAX_SIZES                           */
+    const int* P;            /* n_sizes samples-per-channel values (host)                  */
+    const int* T;            /* n_sizes output lengths (host); each a positive multiple of
+                                its P                                                      */
+    const int64_t* N1;       /* n_sizes band starts (host), or NULL for -floor(M*P/2)      */
+    unsigned out_flags;      /* OR of MCI_OUT_*; 2-D requires exactly MCI_OUT_F            */
+    int precision;           /* MCI_FP32 or MCI_FP64: type of samples and outputs          */
+    int singular_policy;     /* MCI_SINGULAR_*                                             */
+    double singular_rtol;    /* residue singular when sigma_min < rtol * sigma_max;
+                                <= 0 selects 1e-13                                         */
+    int channel_mode;        /* MCI_CHANNELS_*                                             */
+    int64_t max_batch;       /* most signals one mci_interp_1d call passes (>= 1)          */
+    int64_t max_images;      /* most images one mci_upsample_2d call passes (0: no 2-D)    */
+    int64_t max_intermediate;/* most row-pass pixels one mci_upsample_2d call needs:
+                                sum over images of h * s * w (0: no 2-D)                   */
+} mci_desc;
+
+typedef struct {
+    int n_singular;          /* singular residues over all size classes                   */
+    double max_cond;         /* largest sigma_max / sigma_min over non-singular residues  */
+    int device_status;       /* device status word since the last query (0: clean);
+                                bit 0 bad size class, bit 1 bad image size, bit 2 bad
+                                offset / alignment, bit 3 batch above max_batch,
+                                bit 4 intermediate above max_intermediate                 */
+    int signals_per_cta[MCI_MAX_SIZES]; /* tile height chosen per size class              */
+    int threads_per_cta;
+    int smem_bytes;          /* dynamic shared memory per CTA                             */
+    int64_t table_bytes;     /* device bytes of per-residue tables and twiddles           */
+    int64_t workspace_bytes; /* device bytes of the 1-D and 2-D workspace                 */
+} mci_plan_stats;
+
+/*
+ * mci_plan -- build a plan: validate the description, form every per-residue
+ * system matrix H_r[j][k] = b_k(N1 + r + j P) of every size class in FP64
+ * (Eq. (defH)), invert it by a singular value decomposition (pseudo-inverse
+ * or zero or error where singular, Remark (aequal0)), fold the inverse, the
+ * output operator and the evaluation phases into per-bin tables, round them to
+ * the plan's precision and upload them, and allocate the workspace.
+ * *plan receives the plan on success.  Synchronises the stream.  Supported
+ * sizes: P even with P = 2^a (4 <= P <= 8192) or 3 * 2^a (12 <= P <= 6144),
+ * T a multiple of P, and the per-CTA working set within shared memory;
+ * otherwise MCI_ERR_UNSUPPORTED_SIZE.
+ */
+mci_status mci_plan(mci_plan_t* plan, const mci_desc* desc, mci_stream_t stream);
+
+/*
+ * mci_interp_1d -- reconstruct a batch of 1-D signals (Theorem (MCIeq),
+ * Eq. (DFTexpression); operator T_N of Eq. (appxi operator)).
+ *   in         device, samples of signal b: in + in_off[b] holds M_in x P_c values
+ *              (channel-major: channel m at [m * P_c + p]); M_in = M for measured
+ *              channels, 1 for MCI_CHANNELS_FD.  Element type per precision.
+ *   in_off     device int64 element offsets, or NULL: signals packed back to back
+ *   out        device, out + out_off[b] receives n_out x T_c values (n_out = number
+ *              of bits in out_flags), output-major, out[o * T_c + j] = value at
+ *              t_j = 2 pi j / T_c
+ *   out_off    device int64 element offsets, or NULL: packed back to back
+ *   size_class device int per signal (0 .. n_sizes-1), or NULL when n_sizes == 1
+ *   batch      number of signals, 0 .. max_batch
+ * Offsets that are multiples of 4 elements (FP32) or 2 (FP64) take the
+ * vectorised path; others work but run slower.
+ */
+mci_status mci_interp_1d(mci_plan_t plan, const void* in, const int64_t* in_off, void* out,
+                         const int64_t* out_off, const int* size_class, int64_t batch,
+                         mci_stream_t stream);
+
+/*
+ * mci_upsample_2d -- separable 2-D interpolation of Section 5.2: every row of
+ * an h x w image is interpolated from w samples to s*w, then every column of
+ * that h x (s w) intermediate from h samples to s*h.  Channels come from the
+ * plan's channel mode (FD derivatives of the pixel row/column, or M = 1).
+ * The plan must hold a size class (w, s*w) and a class (h, s*h) for every
+ * image (the same class serves both when h == w).
+ *   lr       device float, image i at lr + lr_off[i], h_i x w_i row-major
+ *   lr_off   device int64 element offsets, or NULL (packed)
+ *   h, w     device int arrays of image heights and widths
+ *   scale    device int array of scale factors s_i >= 1
+ *   hr       device float, image i at hr + hr_off[i], (s h) x (s w) row-major
+ *   hr_off   device int64 element offsets, or NULL (packed)
+ *   n_img    number of images, 0 .. max_images
+ * Only MCI_FP32 plans.  Uses the plan's workspace for the intermediate, so
+ * calls on one plan must not overlap on the device.
+ */
+mci_status mci_upsample_2d(mci_plan_t plan, const float* lr, const int64_t* lr_off, const int* h,
+                           const int* w, const int* scale, float* hr, const int64_t* hr_off,
+                           int64_t n_img, mci_stream_t stream);
+
+/* mci_plan_info -- fill *stats; synchronises the plan's last stream to read the
+ * device status word, then clears it. */
+mci_status mci_plan_info(mci_plan_t plan, mci_plan_stats* stats);
+
+/* mci_destroy -- release the plan's device tables, workspace and streams
+ * (synchronises its streams first).  NULL is a no-op. */
+mci_status mci_destroy(mci_plan_t plan);
+
+/* mci_error_string -- static description of a status code. */
+const char* mci_error_string(mci_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCI_H */

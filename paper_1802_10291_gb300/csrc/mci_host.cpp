@@ -1,0 +1,642 @@
+// Host side of the C ABI: plan construction in FP64 and the stream-ordered
+// entry points.  See include/mci.h for the contract of every function.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mci_internal.h"
+
+using cd = std::complex<double>;
+
+namespace mci {
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// e^{2 pi i q / den}, q reduced modulo den in integers first.
+cd cis_frac(int64_t q, int64_t den)
+{
+    q %= den;
+    if (q < 0) q += den;
+    const double a = kTwoPi * (double)q / (double)den;
+    return cd(std::cos(a), std::sin(a));
+}
+
+int sgn(int64_t n) { return (n > 0) - (n < 0); }
+
+// Fourier multiplier b(n) of one system (Eq. (sysfunction); Examples 2, 3, 5).
+cd system_multiplier(const mci_system& s, const double* custom_class, int64_t N1, int64_t n)
+{
+    switch (s.kind) {
+    case MCI_SYS_IDENTITY: return 1.0;
+    case MCI_SYS_DERIV: {
+        cd v = 1.0;
+        for (int i = 0; i < s.order; ++i) v *= cd(0.0, (double)n);
+        return v;
+    }
+    case MCI_SYS_HILBERT: return cd(0.0, -(double)sgn(n));
+    case MCI_SYS_SHIFT: return cd(std::cos((double)n * s.tau), std::sin((double)n * s.tau));
+    case MCI_SYS_CUSTOM: {
+        const int64_t i = n - N1;
+        return cd(custom_class[2 * i], custom_class[2 * i + 1]);
+    }
+    }
+    return 0.0;
+}
+
+// Output operators (Example 6): f, Hilbert transform, derivative.
+cd output_multiplier(int op, int64_t n)
+{
+    if (op == MCI_OUT_HILBERT) return cd(0.0, -(double)sgn(n));
+    if (op == MCI_OUT_DERIV) return cd(0.0, (double)n);
+    return 1.0;
+}
+
+// One-sided (Hestenes) Jacobi SVD of an M x M complex matrix, row-major:
+// on return A holds U * diag(sigma) column-wise, V the right singular vectors.
+void jacobi_svd(int M, std::vector<cd>& A, std::vector<cd>& V)
+{
+    V.assign(M * M, 0.0);
+    for (int i = 0; i < M; ++i) V[i * M + i] = 1.0;
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < M - 1; ++i)
+            for (int j = i + 1; j < M; ++j) {
+                double alpha = 0.0, beta = 0.0;
+                cd gamma = 0.0;
+                for (int r = 0; r < M; ++r) {
+                    alpha += std::norm(A[r * M + i]);
+                    beta += std::norm(A[r * M + j]);
+                    gamma += std::conj(A[r * M + i]) * A[r * M + j];
+                }
+                const double g = std::abs(gamma);
+                if (g == 0.0 || alpha == 0.0 || beta == 0.0) continue;
+                off = std::max(off, g / std::sqrt(alpha * beta));
+                if (g <= 1e-300) continue;
+                const cd ph = gamma / g;  // e^{i phi}
+                const double zeta = (beta - alpha) / (2.0 * g);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::abs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                for (int r = 0; r < M; ++r) {
+                    const cd ai = A[r * M + i], aj = A[r * M + j] * std::conj(ph);
+                    A[r * M + i] = c * ai - s * aj;
+                    A[r * M + j] = s * ai + c * aj;
+                    const cd vi = V[r * M + i], vj = V[r * M + j] * std::conj(ph);
+                    V[r * M + i] = c * vi - s * vj;
+                    V[r * M + j] = s * vi + c * vj;
+                }
+            }
+        if (off < 1e-16) break;
+    }
+}
+
+struct ResidueInverse {
+    std::vector<cd> Q;  // P x M x M: Q[(r*M + m)*M + j], channel m, alias j
+    int n_singular = 0;
+    double max_cond = 1.0;
+};
+
+// H_r[j][k] = b_k(N1 + r + j P) (Eq. (defH)); Q_r = H_r^{-1} or its pseudo-inverse.
+mci_status invert_residues(const mci_desc& d, int P, int64_t N1, const double* const* custom,
+                           double rtol, ResidueInverse& out)
+{
+    const int M = d.M;
+    out.Q.assign((size_t)P * M * M, 0.0);
+    std::vector<cd> H(M * M), V;
+    for (int r = 0; r < P; ++r) {
+        const int64_t n = N1 + r;
+        for (int j = 0; j < M; ++j)
+            for (int k = 0; k < M; ++k)
+                H[j * M + k] = system_multiplier(d.sys[k], custom[k], N1, n + (int64_t)j * P);
+        jacobi_svd(M, H, V);
+        std::vector<double> sig(M);
+        double smax = 0.0;
+        for (int k = 0; k < M; ++k) {
+            double nn = 0.0;
+            for (int row = 0; row < M; ++row) nn += std::norm(H[row * M + k]);
+            sig[k] = std::sqrt(nn);
+            smax = std::max(smax, sig[k]);
+        }
+        double smin = smax;
+        for (int k = 0; k < M; ++k) smin = std::min(smin, sig[k]);
+        const bool singular = !(smax > 0.0) || smin < rtol * smax;
+        if (singular) {
+            ++out.n_singular;
+            if (d.singular_policy == MCI_SINGULAR_ERROR) return MCI_ERR_SINGULAR;
+            if (d.singular_policy == MCI_SINGULAR_ZERO || !(smax > 0.0)) continue;  // Q_r = 0
+        } else {
+            out.max_cond = std::max(out.max_cond, smax / smin);
+        }
+        // pinv(H) = V Sigma^+ U^H, U[:,k] = H[:,k] / sigma_k
+        for (int m = 0; m < M; ++m)
+            for (int j = 0; j < M; ++j) {
+                cd acc = 0.0;
+                for (int k = 0; k < M; ++k) {
+                    if (!(sig[k] > rtol * smax) || sig[k] == 0.0) continue;
+                    const cd u_jk = H[j * M + k] / sig[k];
+                    acc += V[m * M + k] * std::conj(u_jk) / sig[k];
+                }
+                out.Q[((size_t)r * M + m) * M + j] = acc;
+            }
+    }
+    return MCI_OK;
+}
+
+bool supported_p(int P)
+{
+    if (P < 4 || P % 2) return false;
+    int q = P;
+    bool three = false;
+    if (q % 3 == 0) {
+        q /= 3;
+        three = true;
+    }
+    if (q & (q - 1)) return false;  // remaining part must be a power of two
+    if (three) return P >= 12 && P <= 6144;
+    return P <= 8192;
+}
+
+struct HostClass {
+    int P, T, s, N;
+    int64_t N1;
+};
+
+}  // namespace
+}  // namespace mci
+
+using namespace mci;
+
+struct mci_plan_s {
+    mci_desc desc{};
+    std::vector<mci_system> sys;
+    std::vector<HostClass> cls;
+    std::vector<ClassDev> cdev;
+    std::vector<ClassLaunch> launch;  // host copy of d_launch
+    std::vector<const void*> kern;    // per class host kernel (contiguous pattern)
+    std::vector<const void*> kern_cols;
+    std::vector<int> csmem;           // per class dynamic shared memory
+    int n_out = 0;
+    int M_in = 0;
+    int smem = 0;                     // largest per-class shared memory
+    int n_singular = 0;
+    double max_cond = 1.0;
+    std::vector<int> order;           // class ids by descending P
+    size_t elem = 4;                  // sizeof(real)
+    int64_t max_items = 0;            // 2-D work-list capacity
+    // device memory
+    void* d_tables = nullptr;         // launch info | order | tw | W
+    ClassLaunch* d_launch = nullptr;
+    int* d_order = nullptr;
+    void* d_tw = nullptr;
+    void* d_W = nullptr;
+    int64_t table_bytes = 0;
+    void* d_work = nullptr;           // 1-D and 2-D workspace
+    int64_t work_bytes = 0;
+    int* d_status = nullptr;
+    int64_t* d_sorted = nullptr;
+    int64_t* d_in_pref = nullptr;
+    int64_t* d_out_pref = nullptr;
+    Sched1D* d_sched1 = nullptr;
+    float* d_inter = nullptr;
+    int64_t* d_inter_off = nullptr;
+    int64_t* d_lr_pref = nullptr;
+    int64_t* d_hr_pref = nullptr;
+    int* d_row_cls = nullptr;
+    int* d_col_cls = nullptr;
+    int2* d_items = nullptr;
+    Sched2D* d_sched2 = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+mci_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return MCI_OK;
+    if (e == cudaErrorMemoryAllocation) return MCI_ERR_OOM;
+    return MCI_ERR_CUDA;
+}
+
+mci_status validate(const mci_desc* d)
+{
+    if (!d || d->M < 1 || d->M > MCI_MAX_CHANNELS || !d->sys) return MCI_ERR_INVALID_ARG;
+    if (d->n_sizes < 1 || d->n_sizes > MCI_MAX_SIZES || !d->P || !d->T) return MCI_ERR_INVALID_ARG;
+    if (d->out_flags == 0 || (d->out_flags & ~7u)) return MCI_ERR_INVALID_ARG;
+    if (d->precision != MCI_FP32 && d->precision != MCI_FP64) return MCI_ERR_INVALID_ARG;
+    if (d->singular_policy < 0 || d->singular_policy > 2) return MCI_ERR_INVALID_ARG;
+    if (d->channel_mode != MCI_CHANNELS_MEASURED && d->channel_mode != MCI_CHANNELS_FD)
+        return MCI_ERR_INVALID_ARG;
+    if (d->max_batch < 1 || d->max_images < 0 || d->max_intermediate < 0) return MCI_ERR_INVALID_ARG;
+    for (int k = 0; k < d->M; ++k) {
+        const mci_system& s = d->sys[k];
+        if (s.kind < MCI_SYS_IDENTITY || s.kind > MCI_SYS_CUSTOM) return MCI_ERR_INVALID_ARG;
+        if (s.kind == MCI_SYS_DERIV && s.order < 1) return MCI_ERR_INVALID_ARG;
+        if (s.kind == MCI_SYS_CUSTOM && !s.custom) return MCI_ERR_INVALID_ARG;
+        if (d->channel_mode == MCI_CHANNELS_FD) {
+            if (k == 0 && s.kind != MCI_SYS_IDENTITY) return MCI_ERR_INVALID_ARG;
+            if (k > 0 && !(s.kind == MCI_SYS_DERIV && (s.order == 1 || s.order == 2)))
+                return MCI_ERR_INVALID_ARG;
+        }
+    }
+    for (int c = 0; c < d->n_sizes; ++c) {
+        if (!supported_p(d->P[c])) return MCI_ERR_UNSUPPORTED_SIZE;
+        if (d->T[c] < d->P[c] || d->T[c] % d->P[c]) return MCI_ERR_UNSUPPORTED_SIZE;
+        for (int c2 = 0; c2 < c; ++c2)
+            if (d->P[c2] == d->P[c] && d->T[c2] == d->T[c] &&
+                (!d->N1 || d->N1[c2] == d->N1[c]))
+                return MCI_ERR_INVALID_ARG;  // duplicate size class
+    }
+    if (d->max_images > 0 && d->precision != MCI_FP32) return MCI_ERR_INVALID_ARG;
+    if (d->max_images > 0 && d->out_flags != MCI_OUT_F) return MCI_ERR_INVALID_ARG;
+    if (d->max_images > 0 && d->channel_mode == MCI_CHANNELS_MEASURED && d->M != 1)
+        return MCI_ERR_INVALID_ARG;
+    return MCI_OK;
+}
+
+// FD spectral factor of system k on bin k of a length-P real DFT (Section 5.2 centred differences).
+cd fd_factor(const mci_system& s, int P, int k)
+{
+    if (s.kind == MCI_SYS_IDENTITY) return 1.0;
+    const double h = kTwoPi / P;
+    const cd e = cis_frac(k, P);
+    if (s.order == 1) return (e - std::conj(e)) / (2.0 * h);           // i sin(2 pi k/P) / h
+    return (e - 2.0 + std::conj(e)) / (h * h);                          // (2 cos - 2) / h^2
+}
+
+template <typename R>
+void push_cpx(std::vector<R>& v, cd z)
+{
+    v.push_back((R)z.real());
+    v.push_back((R)z.imag());
+}
+
+template <typename R>
+mci_status build_tables(mci_plan_s* p, std::vector<R>& tw, std::vector<R>& W)
+{
+    const mci_desc& d = p->desc;
+    const int M = d.M, Min = p->M_in, nout = p->n_out;
+    const double rtol = d.singular_rtol > 0 ? d.singular_rtol : 1e-13;
+    std::vector<int> ops;
+    for (int o : {MCI_OUT_F, MCI_OUT_HILBERT, MCI_OUT_DERIV})
+        if (d.out_flags & o) ops.push_back(o);
+    size_t custom_off = 0;
+    for (size_t c = 0; c < p->cls.size(); ++c) {
+        const HostClass& hc = p->cls[c];
+        const int P = hc.P, N = hc.N, s = hc.s, T = hc.T, Q = s * nout;
+        std::vector<const double*> custom(M, nullptr);
+        for (int k = 0; k < M; ++k)
+            if (d.sys[k].kind == MCI_SYS_CUSTOM) custom[k] = d.sys[k].custom + custom_off;
+        custom_off += (size_t)2 * M * P;
+        ResidueInverse inv;
+        mci_status st = invert_residues(d, P, hc.N1, custom.data(), rtol, inv);
+        if (st != MCI_OK) return st;
+        p->n_singular += inv.n_singular;
+        p->max_cond = std::max(p->max_cond, inv.max_cond);
+        ClassDev& cd_ = p->cdev[c];
+        cd_.tw_off = (int64_t)(tw.size() / 2);
+        cd_.w_off = (int64_t)(W.size() / 2);
+        for (int q = 0; q < P; ++q) push_cpx(tw, cis_frac(-q, P));
+        // W_r[m][q] = (1/P) sum_j Q_r[m][j] o(n_j) e^{2 pi i n_j u / T}, n_j = N1 + r + j P
+        auto Wfull = [&](int r, int m, int q) {
+            const int o = ops[q / s], u = q % s;
+            cd acc = 0.0;
+            for (int j = 0; j < M; ++j) {
+                const int64_t n = hc.N1 + r + (int64_t)j * P;
+                acc += inv.Q[((size_t)r * M + m) * M + j] * output_multiplier(o, n) *
+                       cis_frac(n * (int64_t)u, T);
+            }
+            return acc / (double)P;
+        };
+        auto res = [&](int k) { return (int)((((int64_t)k - hc.N1) % P + P) % P); };
+        std::vector<cd> Wk((size_t)M * Q);
+        for (int k = 0; k <= N; ++k) {
+            const int ra = res(k), rb = res((P - k) % P);
+            for (int m = 0; m < M; ++m)
+                for (int q = 0; q < Q; ++q)
+                    Wk[(size_t)m * Q + q] = 0.5 * (Wfull(ra, m, q) + std::conj(Wfull(rb, m, q)));
+            if (d.channel_mode == MCI_CHANNELS_FD) {
+                for (int q = 0; q < Q; ++q) {
+                    cd acc = 0.0;
+                    for (int m = 0; m < M; ++m) acc += fd_factor(d.sys[m], P, k) * Wk[(size_t)m * Q + q];
+                    push_cpx(W, acc);
+                }
+            } else {
+                for (int m = 0; m < Min; ++m)
+                    for (int q = 0; q < Q; ++q) push_cpx(W, Wk[(size_t)m * Q + q]);
+            }
+        }
+    }
+    return MCI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mci_error_string(mci_status s)
+{
+    switch (s) {
+    case MCI_OK: return "success";
+    case MCI_ERR_INVALID_ARG: return "invalid argument";
+    case MCI_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case MCI_ERR_SINGULAR: return "singular system matrix";
+    case MCI_ERR_CUDA: return "CUDA runtime error";
+    case MCI_ERR_OOM: return "device out of memory";
+    case MCI_ERR_TIMEOUT: return "device wait timed out";
+    case MCI_ERR_DEVICE: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+mci_status mci_destroy(mci_plan_t p)
+{
+    if (!p) return MCI_OK;
+    cudaDeviceSynchronize();
+    if (p->d_tables) cudaFree(p->d_tables);
+    if (p->d_work) cudaFree(p->d_work);
+    delete p;
+    return MCI_OK;
+}
+
+mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
+{
+    if (!out) return MCI_ERR_INVALID_ARG;
+    *out = nullptr;
+    mci_status st = validate(desc);
+    if (st != MCI_OK) return st;
+    mci_plan_s* p = new (std::nothrow) mci_plan_s();
+    if (!p) return MCI_ERR_OOM;
+    p->desc = *desc;
+    p->sys.assign(desc->sys, desc->sys + desc->M);
+    p->desc.sys = p->sys.data();
+    p->desc.P = nullptr;  // host arrays are not kept
+    p->desc.T = nullptr;
+    p->desc.N1 = nullptr;
+    const mci_desc& d = p->desc;
+    p->elem = d.precision == MCI_FP64 ? 8 : 4;
+    p->M_in = d.channel_mode == MCI_CHANNELS_FD ? 1 : d.M;
+    p->n_out = __builtin_popcount(d.out_flags);
+    const int n = desc->n_sizes;
+    p->cls.resize(n);
+    p->cdev.resize(n);
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        delete p;
+        return MCI_ERR_CUDA;
+    }
+    const int smem_cap = (int)prop.sharedMemPerBlockOptin - 1024;
+    const int csz = (int)(2 * p->elem);
+    int need = 0;
+    int Pmax = 0, Tmax = 0;
+    for (int c = 0; c < n; ++c) {
+        HostClass& hc = p->cls[c];
+        hc.P = desc->P[c];
+        hc.T = desc->T[c];
+        hc.s = hc.T / hc.P;
+        hc.N = hc.P / 2;
+        hc.N1 = desc->N1 ? desc->N1[c] : -(int64_t)((int64_t)d.M * hc.P / 2);
+        Pmax = std::max(Pmax, hc.P);
+        Tmax = std::max(Tmax, hc.T);
+        ClassDev& cd_ = p->cdev[c];
+        cd_.P = hc.P;
+        cd_.N = hc.N;
+        cd_.T = hc.T;
+        cd_.s = hc.s;
+        cd_.M_in = p->M_in;
+        cd_.n_out = p->n_out;
+        cd_.Q = hc.s * p->n_out;
+        cd_.QM = std::max(cd_.M_in, cd_.Q);
+        cd_.npad = padded_len(hc.N);
+        const int per = cd_.QM * cd_.npad * csz;
+        if (per > smem_cap) {
+            delete p;
+            return MCI_ERR_UNSUPPORTED_SIZE;
+        }
+        need = std::max(need, per);
+    }
+    const int budget = std::max(need, std::min(kSmemBudget, smem_cap));
+    p->csmem.resize(n);
+    for (int c = 0; c < n; ++c) {
+        ClassDev& cd_ = p->cdev[c];
+        const int per = cd_.QM * cd_.npad * csz;
+        cd_.G = std::max(1, std::min(kMaxTile, budget / per));
+        p->csmem[c] = cd_.G * per;
+        p->smem = std::max(p->smem, p->csmem[c]);
+    }
+    p->order.resize(n);
+    for (int c = 0; c < n; ++c) p->order[c] = c;
+    std::stable_sort(p->order.begin(), p->order.end(),
+                     [&](int a, int b) { return p->cls[a].P > p->cls[b].P; });
+
+    // FP64 tables
+    std::vector<float> tw32, W32;
+    std::vector<double> tw64, W64;
+    st = d.precision == MCI_FP64 ? build_tables<double>(p, tw64, W64) : build_tables<float>(p, tw32, W32);
+    if (st != MCI_OK) {
+        delete p;
+        return st;
+    }
+    const void* tw_src = d.precision == MCI_FP64 ? (const void*)tw64.data() : (const void*)tw32.data();
+    const void* W_src = d.precision == MCI_FP64 ? (const void*)W64.data() : (const void*)W32.data();
+    const size_t tw_bytes = (d.precision == MCI_FP64 ? tw64.size() : tw32.size()) * p->elem;
+    const size_t W_bytes = (d.precision == MCI_FP64 ? W64.size() : W32.size()) * p->elem;
+    const size_t launch_bytes = align_up(sizeof(ClassLaunch) * n, 256);
+    const size_t order_bytes = align_up(sizeof(int) * n, 256);
+    const size_t total = launch_bytes + order_bytes + align_up(tw_bytes, 256) + align_up(W_bytes, 256);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc(&p->d_tables, total);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_status(e);
+    }
+    p->table_bytes = (int64_t)total;
+    char* base = (char*)p->d_tables;
+    p->d_launch = (ClassLaunch*)base;
+    p->d_order = (int*)(base + launch_bytes);
+    p->d_tw = base + launch_bytes + order_bytes;
+    p->d_W = base + launch_bytes + order_bytes + align_up(tw_bytes, 256);
+    p->launch.resize(n);
+    p->kern.resize(n);
+    p->kern_cols.resize(n);
+    for (int c = 0; c < n; ++c) {
+        ClassLaunch& L = p->launch[c];
+        L.c = p->cdev[c];
+        L.tw = (const char*)p->d_tw + p->cdev[c].tw_off * 2 * p->elem;
+        L.W = (const char*)p->d_W + p->cdev[c].w_off * 2 * p->elem;
+        L.prec = d.precision;
+        L.smem = p->csmem[c];
+        p->kern[c] = kernel_lookup(d.precision, false, p->cdev[c].N);
+        p->kern_cols[c] = d.precision == MCI_FP32 ? kernel_lookup(d.precision, true, p->cdev[c].N) : nullptr;
+        if (!p->kern[c]) e = cudaErrorInvalidDeviceFunction;
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(p->kern[c], cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+        if (e == cudaSuccess && p->kern_cols[c])
+            e = cudaFuncSetAttribute(p->kern_cols[c], cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_launch, p->launch.data(), sizeof(ClassLaunch) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_order, p->order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_tw, tw_src, tw_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_W, W_src, W_bytes, cudaMemcpyHostToDevice, s);
+
+    // workspace
+    const int64_t B = d.max_batch, I = d.max_images, X = d.max_intermediate;
+    p->max_items = I * (int64_t)(Pmax + Tmax);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_status = carve(sizeof(int) * 4);
+    const size_t o_sorted = carve(sizeof(int64_t) * B);
+    const size_t o_inp = carve(sizeof(int64_t) * B);
+    const size_t o_outp = carve(sizeof(int64_t) * B);
+    const size_t o_s1 = carve(sizeof(Sched1D));
+    size_t o_inter = 0, o_ioff = 0, o_lrp = 0, o_hrp = 0, o_rc = 0, o_cc = 0, o_it = 0, o_s2 = 0;
+    if (I > 0) {
+        o_inter = carve(sizeof(float) * (size_t)X);
+        o_ioff = carve(sizeof(int64_t) * I);
+        o_lrp = carve(sizeof(int64_t) * I);
+        o_hrp = carve(sizeof(int64_t) * I);
+        o_rc = carve(sizeof(int) * I);
+        o_cc = carve(sizeof(int) * I);
+        o_it = carve(sizeof(int2) * (size_t)p->max_items);
+        o_s2 = carve(sizeof(Sched2D));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_work, off);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        mci_destroy(p);
+        return cuda_status(e);
+    }
+    p->work_bytes = (int64_t)off;
+    char* w = (char*)p->d_work;
+    p->d_status = (int*)(w + o_status);
+    p->d_sorted = (int64_t*)(w + o_sorted);
+    p->d_in_pref = (int64_t*)(w + o_inp);
+    p->d_out_pref = (int64_t*)(w + o_outp);
+    p->d_sched1 = (Sched1D*)(w + o_s1);
+    if (I > 0) {
+        p->d_inter = (float*)(w + o_inter);
+        p->d_inter_off = (int64_t*)(w + o_ioff);
+        p->d_lr_pref = (int64_t*)(w + o_lrp);
+        p->d_hr_pref = (int64_t*)(w + o_hrp);
+        p->d_row_cls = (int*)(w + o_rc);
+        p->d_col_cls = (int*)(w + o_cc);
+        p->d_items = (int2*)(w + o_it);
+        p->d_sched2 = (Sched2D*)(w + o_s2);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int) * 4, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        mci_destroy(p);
+        return cuda_status(e);
+    }
+    p->last_stream = s;
+    *out = p;
+    return MCI_OK;
+}
+
+mci_status mci_interp_1d(mci_plan_t p, const void* in, const int64_t* in_off, void* out,
+                         const int64_t* out_off, const int* size_class, int64_t batch,
+                         mci_stream_t stream)
+{
+    if (!p || batch < 0 || batch > p->desc.max_batch) return MCI_ERR_INVALID_ARG;
+    if (batch == 0) return MCI_OK;
+    if (!in || !out) return MCI_ERR_INVALID_ARG;
+    const int n = (int)p->cls.size();
+    if (n > 1 && !size_class) return MCI_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    KArgs a{};
+    a.in = in;
+    a.out = out;
+    a.in_off = in_off;
+    a.out_off = out_off;
+    a.batch = batch;
+    a.sorted = p->d_sorted;
+    a.sched1 = p->d_sched1;
+    a.status = p->d_status;
+    cudaError_t e;
+    if (n == 1) {
+        // uniform batch: launched from the host, one CTA per tile
+        a.c = p->cdev[0];
+        a.cls = 0;
+        a.mode = kModeUniform;
+        a.tw = p->launch[0].tw;
+        a.W = p->launch[0].W;
+        const int64_t items = (batch + p->cdev[0].G - 1) / p->cdev[0].G;
+        if (items > 0x7fffffff) return MCI_ERR_UNSUPPORTED_SIZE;
+        a.uniform_items = (int)items;
+        void* args[] = {&a};
+        e = cudaLaunchKernel(p->kern[0], dim3((unsigned)items), dim3(kThreads), args,
+                             (size_t)p->csmem[0], s);
+    } else {
+        e = (cudaError_t)launch_sched_1d(size_class, batch, n, p->d_launch, p->d_order, p->d_sorted,
+                                         p->d_sched1, in_off ? nullptr : p->d_in_pref,
+                                         out_off ? nullptr : p->d_out_pref, a, s);
+    }
+    return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_upsample_2d(mci_plan_t p, const float* lr, const int64_t* lr_off, const int* h,
+                           const int* w, const int* scale, float* hr, const int64_t* hr_off,
+                           int64_t n_img, mci_stream_t stream)
+{
+    if (!p || n_img < 0) return MCI_ERR_INVALID_ARG;
+    if (p->desc.max_images <= 0 || n_img > p->desc.max_images) return MCI_ERR_INVALID_ARG;
+    if (n_img == 0) return MCI_OK;
+    if (!lr || !hr || !h || !w || !scale) return MCI_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    KArgs rows{};
+    rows.in = lr;
+    rows.out = p->d_inter;
+    rows.items = p->d_items;
+    rows.sched2 = p->d_sched2;
+    rows.h = h;
+    rows.w = w;
+    rows.scale = scale;
+    rows.img_in_off = lr_off ? lr_off : p->d_lr_pref;
+    rows.img_out_off = hr_off ? hr_off : p->d_hr_pref;
+    rows.inter_off = p->d_inter_off;
+    rows.status = p->d_status;
+    KArgs cols = rows;
+    cols.in = p->d_inter;
+    cols.out = hr;
+    const int e = launch_sched_2d(n_img, (int)p->cls.size(), p->d_launch, p->desc.max_intermediate,
+                                  p->max_items, p->d_inter_off, lr_off ? nullptr : p->d_lr_pref,
+                                  hr_off ? nullptr : p->d_hr_pref, p->d_row_cls, p->d_col_cls,
+                                  p->d_items, p->d_sched2, rows, cols, s);
+    return e ? MCI_ERR_CUDA : MCI_OK;
+}
+
+mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)
+{
+    if (!p || !st) return MCI_ERR_INVALID_ARG;
+    std::memset(st, 0, sizeof(*st));
+    st->n_singular = p->n_singular;
+    st->max_cond = p->max_cond;
+    for (size_t c = 0; c < p->cdev.size(); ++c) st->signals_per_cta[c] = p->cdev[c].G;
+    st->threads_per_cta = kThreads;
+    st->smem_bytes = p->smem;
+    st->table_bytes = p->table_bytes;
+    st->workspace_bytes = p->work_bytes;
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    st->device_status = status;
+    return cuda_status(e);
+}
+
+}  // extern "C"

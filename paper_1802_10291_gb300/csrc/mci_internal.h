@@ -1,0 +1,117 @@
+// Internal structures shared by the host plan code and the CUDA kernels.
+#pragma once
+#include <stdint.h>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mci.h"
+
+#ifdef __CUDACC__
+#define MCI_HD __host__ __device__
+#else
+#define MCI_HD
+#endif
+
+namespace mci {
+
+constexpr int kThreads = 256;      // threads per CTA of the interpolation kernels
+constexpr int kMaxTile = 64;       // most signals (rows, columns) per CTA tile
+constexpr int kSmemBudget = 64 * 1024;  // preferred dynamic shared memory per CTA
+
+// Padded shared-memory index of complex element e of one FFT buffer: two
+// complex of padding after every 32 keep strided Stockham stores free of bank
+// conflicts and keep even elements 16-byte aligned (vector loads of pairs).
+MCI_HD constexpr int pad16(int e) { return e + 2 * (e >> 5); }
+MCI_HD constexpr int padded_len(int n) { return ((pad16(n) + 1) / 2) * 2; }
+
+// One size class as the kernels see it.
+struct ClassDev {
+    int P;       // samples per channel
+    int N;       // FFT length P/2 (real transforms of length P packed as complex of N)
+    int T;       // output samples
+    int s;       // T / P
+    int M_in;    // channels read from the input (M, or 1 in FD mode)
+    int Q;       // output phases: s * n_out
+    int QM;      // FFT buffers per signal in shared memory: max(M_in, Q)
+    int G;       // signals per tile
+    int n_out;   // outputs per signal
+    int npad;    // padded FFT buffer length (complex elements)
+    int64_t tw_off;  // offset (complex elements) of this class's twiddles e^{-2 pi i q/P}, q < P
+    int64_t w_off;   // offset of this class's bin weights W[k][m][q], k = 0..N
+};
+
+// Device-built grouping of one mci_interp_1d call (uneven batches).
+struct Sched1D {
+    int start[MCI_MAX_SIZES];          // first position of each class in the sorted list
+    int count[MCI_MAX_SIZES];          // signals per class
+};
+
+// What the device-side scheduler needs to launch one size class.
+struct ClassLaunch {
+    ClassDev c;
+    const void* tw;
+    const void* W;
+    int prec;
+    int smem;
+};
+
+enum StatusBits {
+    kStatusBadClass = 1,
+    kStatusBadImage = 2,
+    kStatusBadOffset = 4,
+    kStatusBatch = 8,
+    kStatusIntermediate = 16,
+    kStatusLaunch = 32,
+};
+
+// Device-built work lists of one mci_upsample_2d call: per size class, the
+// row-pass and column-pass items (image, tile) in one list.
+struct Sched2D {
+    int row_start[MCI_MAX_SIZES];
+    int row_count[MCI_MAX_SIZES];
+    int col_start[MCI_MAX_SIZES];
+    int col_count[MCI_MAX_SIZES];
+};
+
+enum KernelMode { kModeUniform = 0, kModeSorted = 1, kModeRows = 2, kModeCols = 3 };
+
+// Arguments of one size-class launch (passed by value).
+struct KArgs {
+    ClassDev c;              // this launch's size class
+    int cls;                 // its index
+    int mode;                // KernelMode
+    const void* in;          // 1-D: samples; rows: LR images; cols: intermediate
+    void* out;               // 1-D: outputs; rows: intermediate; cols: HR images
+    const void* tw;          // this class's twiddles (cpx<R>)
+    const void* W;           // this class's bin weights (cpx<R>)
+    // 1-D
+    const int64_t* in_off;   // per signal, or NULL (packed)
+    const int64_t* out_off;
+    int64_t batch;
+    int uniform_items;
+    const int64_t* sorted;   // signals sorted by class
+    const Sched1D* sched1;
+    // 2-D
+    const int2* items;       // (image, tile) lists of all classes
+    const Sched2D* sched2;
+    const int* h;
+    const int* w;
+    const int* scale;
+    const int64_t* img_in_off;   // LR image offsets
+    const int64_t* img_out_off;  // HR image offsets
+    const int64_t* inter_off;    // intermediate image offsets
+    int* status;
+};
+
+// Kernel for (precision, column pattern, FFT length), or NULL when not compiled.
+const void* kernel_lookup(int precision, bool cols, int N);
+
+int launch_sched_1d(const int* size_class, int64_t batch, int n_classes, const ClassLaunch* cl,
+                    const int* order, int64_t* sorted, Sched1D* st, int64_t* in_pref,
+                    int64_t* out_pref, const KArgs& tmpl, void* stream);
+int launch_sched_2d(int64_t n_img, int n_classes, const ClassLaunch* cl, int64_t max_inter,
+                    int64_t max_items, int64_t* inter_off, int64_t* lr_pref, int64_t* hr_pref,
+                    int* row_cls, int* col_cls, int2* items, Sched2D* st, const KArgs& rows_tmpl,
+                    const KArgs& cols_tmpl, void* stream);
+
+}  // namespace mci

@@ -1,0 +1,209 @@
+// The fused per-tile interpolation pipeline (Eq. (DFTexpression) of Cheng & Kou).
+//
+// A tile holds G signals of one size class in shared memory.  For every signal:
+//   1. its M_in real channels (P samples each) are read as N = P/2 complex
+//      values (even sample = real part, odd sample = imaginary part);
+//   2. forward FFT of length N per channel;
+//   3. per bin pair (k, N-k), k = 0..N/2: the real-input spectrum X_m[k] of
+//      every channel (the even/odd split of a length-P real DFT), then
+//      Y_q[k] = sum_m X_m[k] W[k][m][q] for every output phase q = (o, u), and
+//      the packing of the Hermitian spectrum Y_q into N complex values whose
+//      inverse FFT gives the real output samples 2l, 2l+1 of phase q;
+//   4. inverse FFT of length N per phase;
+//   5. phase u of output o holds the samples j = s l + u of the T-grid.
+// W[k][m][q] already contains the per-residue inverse system matrix
+// (Eq. (matrixeqn1)), the output operator, the phase e^{i n 2 pi u / T} of
+// sub-grid u, the 1/P of the DFT, and the Hermitian symmetrisation that makes
+// the output the real part of the interpolant; it is built in FP64 by the
+// plan.  The spectrum never leaves shared memory.
+#pragma once
+#include "fft_device.cuh"
+
+namespace mci {
+
+template <typename R>
+__device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int gcount,
+                                          const cpx<R>* __restrict__ tw,
+                                          const cpx<R>* __restrict__ W)
+{
+    const int npad = c.npad, QM = c.QM, Min = c.M_in, Q = c.Q, N = c.N;
+    const int NH = N / 2;
+    const int total = (NH + 1) * gcount;
+    for (int it = ltid(); it < total; it += blockDim.x) {
+        const int g = it % gcount;
+        const int k = it / gcount;
+        const int kk = (N - k) % N;  // mirror bin (k = 0 pairs with bin N == 0 of Z)
+        cpx<R>* base = sm + g * QM * npad;
+        const cpx<R> w = tw[k];      // e^{-2 pi i k / P}
+        cpx<R> Xa[MCI_MAX_CHANNELS], Xb[MCI_MAX_CHANNELS];
+#pragma unroll
+        for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
+            if (m < Min) {
+                const cpx<R> zk = base[m * npad + pad16(k)];
+                const cpx<R> zn = base[m * npad + pad16(kk)];
+                if (k == 0) {
+                    Xa[m] = mk<R>(zk.x + zk.y, R(0));  // X[0]
+                    Xb[m] = mk<R>(zk.x - zk.y, R(0));  // X[N]
+                } else {
+                    const cpx<R> e = scale(zk + conjc(zn), R(0.5));
+                    const cpx<R> d = zk - conjc(zn);
+                    const cpx<R> o = mk<R>(R(0.5) * d.y, R(-0.5) * d.x);  // d / (2i)
+                    const cpx<R> wo = cmul(w, o);
+                    Xa[m] = e + wo;                 // X[k]
+                    Xb[m] = conjc(e - wo);          // X[N-k]
+                }
+            }
+        }
+        const cpx<R>* Wa = W + (int64_t)k * Min * Q;
+        const cpx<R>* Wb = W + (int64_t)(N - k) * Min * Q;
+        for (int q = 0; q < Q; ++q) {
+            cpx<R> ya = mk<R>(0, 0), yb = mk<R>(0, 0);
+#pragma unroll
+            for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
+                if (m < Min) {
+                    ya = ya + cmul(Xa[m], Wa[m * Q + q]);
+                    yb = yb + cmul(Xb[m], Wb[m * Q + q]);
+                }
+            }
+            // pack: Z'[k] = A + iC, Z'[N-k] = conj(A) + i conj(C),
+            // A = Y[k] + conj Y[N-k], C = e^{2 pi i k / P} (Y[k] - conj Y[N-k])
+            const cpx<R> A = ya + conjc(yb);
+            const cpx<R> C = cmulc(ya - conjc(yb), w);
+            base[q * npad + pad16(k)] = mk<R>(A.x - C.y, A.y + C.x);
+            if (k != 0 && k != NH) base[q * npad + pad16(kk)] = mk<R>(A.x + C.y, C.x - A.y);
+        }
+    }
+}
+
+// Buffer f of a tile with `cnt` transforms per signal: signal f / cnt, slot f % cnt.
+struct SlotBase {
+    int cnt, QM, npad;
+    __device__ __forceinline__ int operator()(int f) const
+    {
+        const int g = f / cnt;
+        return (g * QM + (f - g * cnt)) * npad;
+    }
+};
+
+template <typename R, int N>
+__device__ __forceinline__ void compute_tile(cpx<R>* sm, const ClassDev& c, int gcount,
+                                             const cpx<R>* __restrict__ tw,
+                                             const cpx<R>* __restrict__ W)
+{
+    fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad}, tw);
+    combine_tile<R>(sm, c, gcount, tw, W);
+    __syncthreads();
+    fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.QM, c.npad}, tw);
+}
+
+// ---------------------------------------------------------------------------
+// loads and stores
+// ---------------------------------------------------------------------------
+
+// Contiguous signals: signal g's M_in x P samples start at in + off[g].
+template <typename R>
+__device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const R* __restrict__ in,
+                                            const int64_t* off, int gcount)
+{
+    const int P = c.P, Min = c.M_in, npad = c.npad, QM = c.QM;
+    const int per = Min * P;
+    constexpr int VW = sizeof(R) == 4 ? 4 : 2;  // reals per 16-byte vector
+    for (int g = 0; g < gcount; ++g) {
+        const R* src = in + off[g];
+        cpx<R>* dst = sm + g * QM * npad;
+        const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (P % VW == 0);
+        if (vec) {
+            for (int t = ltid(); t < per / VW; t += blockDim.x) {
+                const int i = t * VW;
+                const int m = i / P, p = (i - m * P) >> 1;
+                if constexpr (sizeof(R) == 4) {
+                    const float4 v = __ldg(reinterpret_cast<const float4*>(src) + t);
+                    *reinterpret_cast<float4*>(&dst[m * npad + pad16(p)]) = v;
+                } else {
+                    const double2 v = __ldg(reinterpret_cast<const double2*>(src) + t);
+                    *reinterpret_cast<double2*>(&dst[m * npad + pad16(p)]) = v;
+                }
+            }
+        } else {
+            for (int i = ltid(); i < per; i += blockDim.x) {
+                const int m = i / P, pp = i - m * P;
+                R* d = reinterpret_cast<R*>(&dst[m * npad + pad16(pp >> 1)]);
+                d[pp & 1] = src[i];
+            }
+        }
+    }
+}
+
+// Contiguous outputs: output o of signal g at out + off[g] + o * T, T = s P samples;
+// sample j = s * (2l + e) + u is component e of phase (o, u) at position l.
+template <typename R>
+__device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
+                                             const int64_t* off, int gcount)
+{
+    const int T = c.T, s = c.s, npad = c.npad, QM = c.QM, nout = c.n_out;
+    const int per = nout * T;
+    for (int g = 0; g < gcount; ++g) {
+        R* dst = out + off[g];
+        const cpx<R>* srcs = sm + g * QM * npad;
+        const bool vec = ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && (T % 4 == 0);
+        if (vec) {
+            for (int t = ltid(); t < per / 4; t += blockDim.x) {
+                const int i0 = t * 4;
+                const int o = i0 / T;
+                const int x0 = i0 - o * T;
+                R v[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int x = x0 + e;
+                    const int l2 = x / s, u = x - l2 * s;
+                    const cpx<R> z = srcs[(o * s + u) * npad + pad16(l2 >> 1)];
+                    v[e] = (l2 & 1) ? z.y : z.x;
+                }
+                if constexpr (sizeof(R) == 4) {
+                    reinterpret_cast<float4*>(dst)[t] = make_float4(v[0], v[1], v[2], v[3]);
+                } else {
+                    reinterpret_cast<double2*>(dst)[2 * t] = make_double2(v[0], v[1]);
+                    reinterpret_cast<double2*>(dst)[2 * t + 1] = make_double2(v[2], v[3]);
+                }
+            }
+        } else {
+            for (int i = ltid(); i < per; i += blockDim.x) {
+                const int o = i / T, x = i - o * T;
+                const int l2 = x / s, u = x - l2 * s;
+                const cpx<R> z = srcs[(o * s + u) * npad + pad16(l2 >> 1)];
+                dst[i] = (l2 & 1) ? z.y : z.x;
+            }
+        }
+    }
+}
+
+// Strided signals (image columns): signal g's sample p at in[base + g + p * ld]
+// (one channel).  Consecutive g are adjacent in memory, so threads run over g fastest.
+template <typename R>
+__device__ __forceinline__ void load_cols(cpx<R>* sm, const ClassDev& c, const R* __restrict__ in,
+                                          int64_t base, int64_t ld, int gcount)
+{
+    const int P = c.P, npad = c.npad, QM = c.QM;
+    const int total = P * gcount;
+    for (int i = ltid(); i < total; i += blockDim.x) {
+        const int p = i / gcount, g = i - p * gcount;
+        R* d = reinterpret_cast<R*>(&sm[g * QM * npad + pad16(p >> 1)]);
+        d[p & 1] = __ldg(in + base + g + (int64_t)p * ld);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_cols(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
+                                           int64_t base, int64_t ld, int gcount)
+{
+    const int T = c.T, s = c.s, npad = c.npad, QM = c.QM;
+    const int total = T * gcount;
+    for (int i = ltid(); i < total; i += blockDim.x) {
+        const int x = i / gcount, g = i - x * gcount;
+        const int l2 = x / s, u = x - l2 * s;
+        const cpx<R> z = sm[(g * QM + u) * npad + pad16(l2 >> 1)];
+        out[base + g + (int64_t)x * ld] = (l2 & 1) ? z.y : z.x;
+    }
+}
+
+}  // namespace mci

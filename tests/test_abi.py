@@ -1,0 +1,60 @@
+"""The C ABI library builds, loads and exports every function include/mci.h declares;
+host-side argument validation (no GPU needed)."""
+import ctypes
+
+import pytest
+
+from paper_1802_10291_gb300 import mci
+
+
+def test_exports_every_declared_symbol(mci_lib):
+    declared = mci.header_functions()
+    assert set(declared) == {"mci_plan", "mci_interp_1d", "mci_upsample_2d", "mci_plan_info",
+                             "mci_destroy", "mci_error_string"}
+    for name in declared:
+        assert hasattr(mci_lib, name), name
+
+
+def test_error_strings(mci_lib):
+    for code in range(-7, 1):
+        s = mci.error_string(code)
+        assert s and s != "unknown status"
+    assert mci.error_string(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(systems=[], P=16, T=64), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)] * 9, P=16, T=64), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=10, T=40), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[("identity",)], P=16, T=40), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[("identity",)], P=16384, T=16384), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[("identity",)], P=6, T=12), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[("identity",), ("hilbert",)], P=16, T=64, channels="fd"), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("deriv", 1)], P=16, T=64, channels="fd"), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=[16, 16], T=[64, 64]), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=64, max_batch=0), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=64, max_images=2, max_intermediate=100,
+          outputs=("f", "hilbert")), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=64, max_images=2, max_intermediate=100,
+          precision="fp64"), mci.MCI_ERR_INVALID_ARG),
+])
+def test_plan_validation(mci_lib, kw, status):
+    kw.setdefault("max_batch", 4)
+    d = mci.make_desc(**kw)
+    h = ctypes.c_void_p()
+    assert mci_lib.mci_plan(ctypes.byref(h), ctypes.byref(d), None) == status
+    assert h.value is None
+
+
+def test_null_arguments(mci_lib):
+    assert mci_lib.mci_plan(None, None, None) == mci.MCI_ERR_INVALID_ARG
+    assert mci_lib.mci_interp_1d(None, None, None, None, None, None, 1, None) == mci.MCI_ERR_INVALID_ARG
+    assert mci_lib.mci_upsample_2d(None, None, None, None, None, None, None, None, 1, None) == \
+        mci.MCI_ERR_INVALID_ARG
+    assert mci_lib.mci_plan_info(None, None) == mci.MCI_ERR_INVALID_ARG
+    assert mci_lib.mci_destroy(None) == mci.MCI_OK
+
+
+def test_product_refuses_without_library(tmp_path):
+    with pytest.raises(ImportError):
+        mci._open(str(tmp_path / "missing.so"))

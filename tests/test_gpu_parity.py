@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 path max-abs error <= 1e-12 on unit-scale signals; FP32 path
+max-abs error <= 1e-5 x RMS of the oracle output (relative to signal RMS).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1802_10291_gb300 import mci
+from paper_1802_10291_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+F, H, D1, D2 = ("identity",), ("hilbert",), ("deriv", 1), ("deriv", 2)
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+def run_1d(g, systems, T, prec, outputs=("f",), N1=None, **kw):
+    batch, M_in, P = g.shape
+    plan = mci.Plan(systems, P, T, outputs=outputs, precision=prec, max_batch=batch,
+                    N1=N1, **kw)
+    x = torch.tensor(g, dtype=DT[prec], device="cuda")
+    y = torch.full((batch, len(outputs), T), float("nan"), dtype=DT[prec], device="cuda")
+    plan.interp_1d(x, y)
+    torch.cuda.synchronize()
+    info = plan.info()
+    plan.close()
+    assert info["device_status"] == 0
+    return y.cpu().double().numpy()
+
+
+def check(out, ref, prec):
+    assert np.all(np.isfinite(out))
+    if prec == "fp64":
+        err = np.max(np.abs(out - ref))
+        assert err <= TOL[prec] * max(1.0, np.max(np.abs(ref))), err
+    else:
+        err = np.max(np.abs(out - ref)) / np.sqrt(np.mean(ref ** 2))
+        assert err <= TOL[prec], err
+    return err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_exactness_m2_p64_t4096(cuda_device, prec):
+    """M = 2 {f, f'}, P = 64, band {-64..63} with a(-64) = 0, f and Hf at T = 4096."""
+    systems = [F, D1]
+    band = S.band_of(2, 64)
+    a = S.trig_poly(S.rng_for(0), band, 5)
+    g = S.channel_samples(a, band, systems, 64)
+    out = run_1d(g, systems, 4096, prec, outputs=("f", "hilbert"))
+    ref = O.mci_direct(systems, g, 4096, outputs=("f", "hilbert"))
+    check(out, ref, prec)
+    truth = np.stack([[O.truth_from_coeffs(a[b], band, 4096, o) for o in ("f", "hilbert")]
+                      for b in range(5)])
+    check(out, truth, prec)
+
+
+CASES = [
+    ([F], 4, 2), ([F], 8, 3), ([F], 12, 2), ([F], 16, 1), ([F, D1], 32, 4), ([F, H, D1], 64, 4),
+    ([F, D1, D2], 48, 2), ([F, H], 96, 3), ([F, ("shift", 0.4)], 24, 2), ([D1, F], 128, 2),
+    ([F, H, D1], 256, 4), ([F], 384, 2), ([F, D1], 768, 2), ([F, H, D1], 1024, 4),
+    ([F, H, D1], 2048, 4), ([F, H, D1], 4096, 4), ([F, D1], 1536, 2), ([F], 8192, 1),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("systems,P,s", CASES, ids=lambda v: str(v))
+def test_random_samples(cuda_device, prec, systems, P, s):
+    """Arbitrary (not bandlimited) samples; batch with a ragged last tile; f, Hf, f'."""
+    rng = S.rng_for(1, P * 7 + s)
+    M = len(systems)
+    batch = 3 + (4096 // P if P <= 4096 else 1) + 1
+    g = rng.standard_normal((batch, M, P))
+    T = s * P
+    outs = ("f", "hilbert", "deriv") if P <= 2048 else ("f", "hilbert")
+    try:
+        out = run_1d(g, systems, T, prec, outputs=outs)
+    except mci.MciError as e:
+        assert e.status == mci.MCI_ERR_UNSUPPORTED_SIZE and P * len(outs) * s > 8192
+        pytest.skip("working set larger than shared memory")
+    sel = np.unique(np.r_[0, 1, batch - 1])
+    ref = O.mci_direct(systems, g[sel], T, outputs=outs)
+    check(out[sel], ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_smooth_periodic_non_bandlimited(cuda_device, prec):
+    systems = [F, H, D1]
+    g, _, _ = S.signal_batch_1d(S.rng_for(1, 5), 512, 6, systems, "smooth")
+    out = run_1d(g, systems, 2048, prec, outputs=("f", "hilbert"))
+    ref = O.mci_direct(systems, g, 2048, outputs=("f", "hilbert"))
+    check(out, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_singular_residue_policies(cuda_device, prec):
+    """M = 3 {f, Hf, f'} on {-3P/2 .. 3P/2 - 1}: one singular residue (n = -P)."""
+    systems = [F, H, D1]
+    P = 64
+    g = S.rng_for(1, 9).standard_normal((4, 3, P))
+    for policy in ("pinv", "zero"):
+        out = run_1d(g, systems, 4 * P, prec, singular=policy)
+        ref = O.mci_direct(systems, g, 4 * P, policy=policy)
+        check(out, ref, prec)
+    plan = mci.Plan(systems, P, 4 * P, precision=prec, max_batch=1)
+    assert plan.info()["n_singular"] == 1
+    plan.close()
+    with pytest.raises(mci.MciError) as ei:
+        mci.Plan(systems, P, 4 * P, precision=prec, max_batch=1, singular="error")
+    assert ei.value.status == mci.MCI_ERR_SINGULAR
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_band_offsets(cuda_device, prec):
+    systems = [F, D1]
+    P = 32
+    g = S.rng_for(1, 10).standard_normal((3, 2, P))
+    for N1 in (-64, -40, 0, 17):
+        out = run_1d(g, systems, 2 * P, prec, N1=N1, outputs=("f", "deriv"))
+        ref = O.mci_direct(systems, g, 2 * P, N1=N1, outputs=("f", "deriv"))
+        check(out, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fd_channels(cuda_device, prec):
+    """One measured channel, derivative channels from centred differences (Section 5.2)."""
+    for systems in ([F, D1], [F, D1, D2]):
+        x = S.rng_for(1, 11).standard_normal((5, 1, 128))
+        out = run_1d(x, systems, 512, prec, channels="fd")
+        ref = O.mci_direct(systems, O.fd_channels(x[:, 0], systems), 512)
+        check(out, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("packed", [True, False])
+def test_uneven_batch(cuda_device, prec, packed):
+    """Signals of several sizes in one call; device-side grouping and per-class launches."""
+    systems = [F, H, D1]
+    Ps = [256, 64, 512, 24]
+    rng = S.rng_for(1, 12)
+    batch = 41
+    cls = rng.integers(0, len(Ps), batch)
+    cls[:4] = [0, 1, 2, 3]
+    gs = [rng.standard_normal((3, Ps[c])) for c in cls]
+    T = [4 * p for p in Ps]
+    plan = mci.Plan(systems, Ps, T, outputs=("f", "hilbert"), precision=prec, max_batch=batch)
+    in_len = [3 * Ps[c] for c in cls]
+    out_len = [2 * T[c] for c in cls]
+    pad = 0 if packed else 8
+    in_off = np.cumsum([0] + [n + pad for n in in_len])[:-1]
+    out_off = np.cumsum([0] + [n + pad for n in out_len])[:-1]
+    flat = np.zeros(in_off[-1] + in_len[-1] + pad)
+    for b in range(batch):
+        flat[in_off[b]:in_off[b] + in_len[b]] = gs[b].ravel()
+    x = torch.tensor(flat, dtype=DT[prec], device="cuda")
+    y = torch.full((int(out_off[-1] + out_len[-1] + pad),), float("nan"), dtype=DT[prec], device="cuda")
+    sc = torch.tensor(cls, dtype=torch.int32, device="cuda")
+    io = None if packed else torch.tensor(in_off, dtype=torch.int64, device="cuda")
+    oo = None if packed else torch.tensor(out_off, dtype=torch.int64, device="cuda")
+    mci.mci_interp_1d(plan.handle, x, io, y, oo, sc, batch)
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    yh = y.cpu().double().numpy()
+    for b in range(batch):
+        ref = O.mci_direct(systems, gs[b], T[cls[b]], outputs=("f", "hilbert"))
+        got = yh[out_off[b]:out_off[b] + out_len[b]].reshape(2, T[cls[b]])
+        check(got, ref, prec)
+    plan.close()
+
+
+def test_bad_size_class_sets_status(cuda_device):
+    plan = mci.Plan([F], [16, 32], [32, 64], max_batch=4)
+    x = torch.zeros(200, device="cuda")
+    y = torch.zeros(400, device="cuda")
+    sc = torch.tensor([0, 1, 7, -1], dtype=torch.int32, device="cuda")
+    mci.mci_interp_1d(plan.handle, x, None, y, None, sc, 4)
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] & 1
+    assert plan.info()["device_status"] == 0   # cleared by the previous query
+    plan.close()
+
+
+def test_empty_batch_is_noop(cuda_device):
+    plan = mci.Plan([F], 16, 32, max_batch=4)
+    mci.mci_interp_1d(plan.handle, 0, None, 0, None, None, 0)
+    with pytest.raises(mci.MciError):
+        mci.mci_interp_1d(plan.handle, 0, None, 0, None, None, 5)   # above max_batch
+    plan.close()
+
+
+def test_upsample_2d_matches_oracle(cuda_device):
+    """Rows then columns (Section 5.2), FD derivative channel, images of different sizes."""
+    systems = [F, D1]
+    shapes = [(16, 16, 2), (32, 16, 4), (12, 24, 3), (16, 32, 2)]
+    sizes = sorted({(w, s * w) for h, w, s in shapes} | {(h, s * h) for h, w, s in shapes})
+    plan = mci.Plan(systems, [p for p, _ in sizes], [t for _, t in sizes], channels="fd",
+                    max_batch=1, max_images=len(shapes),
+                    max_intermediate=sum(h * s * w for h, w, s in shapes))
+    rng = S.rng_for(2, 3)
+    imgs = [rng.random((h, w)) for h, w, s in shapes]
+    lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), dtype=torch.float32, device="cuda")
+    hr_len = [s * s * h * w for h, w, s in shapes]
+    hr = torch.full((sum(hr_len),), float("nan"), device="cuda")
+    hh = torch.tensor([h for h, w, s in shapes], dtype=torch.int32, device="cuda")
+    ww = torch.tensor([w for h, w, s in shapes], dtype=torch.int32, device="cuda")
+    ss = torch.tensor([s for h, w, s in shapes], dtype=torch.int32, device="cuda")
+    plan.upsample_2d(lr, hh, ww, ss, hr, len(shapes))
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    out = hr.cpu().double().numpy()
+    pos = 0
+    for (h, w, s), im in zip(shapes, imgs):
+        ref = O.upsample_2d(im.astype(np.float32).astype(np.float64), s, systems)
+        got = out[pos:pos + s * s * h * w].reshape(s * h, s * w)
+        pos += s * s * h * w
+        check(got, ref, "fp32")
+    plan.close()
