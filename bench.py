@@ -1,0 +1,386 @@
+"""Benchmark: batched 1-D FFT multichannel interpolation on GB300.
+
+Workload (one step = one mci_interp_1d call over the whole batch):
+16384 signals, M = 3 channels {identity, Hilbert, derivative}, P drawn
+uniformly from {256, 512, 1024, 2048, 4096} per signal, T = 4P output
+samples, half trigonometric polynomials over the band {-3P/2 .. 3P/2 - 1},
+half exp(a cos(t - phi)) (synthetic, seeded).  FP32 is the headline; the FP64
+path runs the same batch for the FP32-vs-FP64 comparison.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank processes its own batch (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MCI output Msamples/s & HR Mpixel/s, FP32 vs FP64 GPU at stated err; % HBM peak"
+UNIT = "Msamples/s"
+SYSTEMS = [("identity",), ("hilbert",), ("deriv", 1)]
+P_CHOICES = [256, 512, 1024, 2048, 4096]
+N_SIGNALS = 16384
+S_FACTOR = 4
+WORKLOAD = ("batched 1-D MCI: 16384 signals, M=3 {identity, Hilbert -i sgn, derivative i n}, "
+            "P ~ U{256,512,1024,2048,4096}, T=4P, half trig polynomials, half exp(a cos(t-phi))")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_batch(rank: int):
+    from paper_1802_10291_gb300 import synth
+    rng = synth.rng_for(1, 1000 + rank)
+    b = synth.uneven_batch_1d(rng, N_SIGNALS, P_CHOICES, SYSTEMS)
+    P_of = b["P"]
+    cls = np.searchsorted(np.asarray(P_CHOICES), P_of).astype(np.int32)
+    flat = np.concatenate([g.ravel() for g in b["g"]])
+    in_len = 3 * P_of
+    out_len = S_FACTOR * P_of
+    in_off = np.concatenate([[0], np.cumsum(in_len)[:-1]]).astype(np.int64)
+    out_off = np.concatenate([[0], np.cumsum(out_len)[:-1]]).astype(np.int64)
+    return dict(P=P_of, cls=cls, flat=flat, g=b["g"], kind=b["kind"], in_off=in_off,
+                out_off=out_off, n_in=int(in_len.sum()), n_out=int(out_len.sum()))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_sample(batch, n_per_class=2, seed=0):
+    """Indices of a stratified sample: n_per_class signals of every P (half of each kind)."""
+    rng = np.random.default_rng(seed)
+    idx = []
+    for P in P_CHOICES:
+        for kind in ("trig", "smooth"):
+            cand = np.nonzero((batch["P"] == P) & (batch["kind"] == kind))[0]
+            k = max(1, n_per_class // 2)
+            idx.extend(rng.choice(cand, size=min(k, cand.size), replace=False).tolist())
+    return sorted(idx)
+
+
+def run_oracle(batch, idx):
+    """FP64 oracle (direct sum formula) on the signals idx; returns {b: [1, T]} and seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    res = {}
+    for P in P_CHOICES:
+        sel = [b for b in idx if batch["P"][b] == P]
+        if not sel:
+            continue
+        g = np.stack([batch["g"][b] for b in sel])
+        out = oracle.mci_direct(SYSTEMS, g, S_FACTOR * P)
+        for i, b in enumerate(sel):
+            res[b] = out[i]
+    return res, time.perf_counter() - t0
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    batch = make_batch(0)
+    classes = list(range(len(P_CHOICES)))
+    rotate = (args.steps + args.warmup) > 40
+    times, outs = [], 0
+    for step in range(args.warmup + args.steps):
+        if rotate:
+            P = P_CHOICES[step % len(P_CHOICES)]
+            idx = [int(np.nonzero(batch["P"] == P)[0][step % 7])]
+        else:
+            idx = [int(np.nonzero(batch["P"] == P)[0][step % 7]) for P in P_CHOICES]
+        _, dt = run_oracle(batch, idx)
+        if step >= args.warmup:
+            times.append(dt)
+            outs += sum(S_FACTOR * int(batch["P"][b]) for b in idx)
+    total = sum(times)
+    value = outs / total / 1e6
+    cores = os.cpu_count()
+    sample = ("per step one signal of every P class (rotating one class per step when more than "
+              "40 steps run), FP64 direct sum formula with tabulated interpolating functions")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the FP32 step (for launch lists under a profiler)")
+    ap.add_argument("--case", default=None, choices=["kernel4096"],
+                    help="profiling case: the P=4096 size-class kernel alone on 3277 signals")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1802_10291_gb300 import mci
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    batch = make_batch(rank)
+    n_cls = len(P_CHOICES)
+    T = [S_FACTOR * p for p in P_CHOICES]
+    stream = torch.cuda.current_stream()
+
+    def setup(prec):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        plan = mci.Plan(SYSTEMS, P_CHOICES, T, precision=prec, max_batch=N_SIGNALS)
+        x = torch.tensor(batch["flat"], dtype=dt, device=dev)
+        y = torch.empty(batch["n_out"], dtype=dt, device=dev)
+        sc = torch.tensor(batch["cls"], device=dev)
+        return plan, x, y, sc
+
+    def step(plan, x, y, sc):
+        mci.mci_interp_1d(plan.handle, x, None, y, None, sc, N_SIGNALS, stream)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, clk.summary()
+
+    if args.case == "kernel4096":
+        sel = np.nonzero(batch["P"] == 4096)[0]
+        g4 = torch.tensor(np.stack([batch["g"][b] for b in sel]), dtype=torch.float32, device=dev)
+        y4 = torch.empty((sel.size, 1, S_FACTOR * 4096), dtype=torch.float32, device=dev)
+        plan4 = mci.Plan(SYSTEMS, 4096, S_FACTOR * 4096, max_batch=sel.size)
+        s4, _ = timed(lambda: plan4.interp_1d(g4, y4), args.steps, args.warmup)
+        print(json.dumps({"case": args.case, "signals": int(sel.size),
+                          "ms_per_launch": 1e3 * s4 / args.steps}), flush=True)
+        return
+
+    # ---- FP32 headline
+    plan32, x32, y32, sc = setup("fp32")
+    info = plan32.info()
+    secs, clocks = timed(lambda: step(plan32, x32, y32, sc), args.steps, args.warmup)
+    secs = max_over_ranks(secs, world)
+    out_samples = batch["n_out"] * world
+    value = out_samples * args.steps / secs / 1e6
+    st = plan32.info()
+    assert st["device_status"] == 0, st
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "value": value, "unit": UNIT,
+                              "ms_per_step": 1e3 * secs / args.steps}), flush=True)
+        return
+
+    # roofline of the step's interpolation kernels: algorithmic bytes = samples in + out
+    hbm, peak_kind = peaks()
+    bytes_step = 4 * (batch["n_in"] + batch["n_out"])
+    achieved = bytes_step * args.steps / (secs) / 1e9
+
+    # dominant kernel alone: the P = 4096 tiles as a uniform batch, host-launched
+    sel = np.nonzero(batch["P"] == 4096)[0]
+    g4 = torch.tensor(np.stack([batch["g"][b] for b in sel]), dtype=torch.float32, device=dev)
+    y4 = torch.empty((sel.size, 1, S_FACTOR * 4096), dtype=torch.float32, device=dev)
+    plan4 = mci.Plan(SYSTEMS, 4096, S_FACTOR * 4096, max_batch=sel.size)
+    s4, _ = timed(lambda: plan4.interp_1d(g4, y4), max(20, args.steps // 4), 3)
+    k_bytes = 4 * (3 * 4096 + S_FACTOR * 4096) * sel.size
+    k_ms = 1e3 * s4 / max(20, args.steps // 4)
+    k_achieved = k_bytes / (k_ms / 1e3) / 1e9
+
+    # ---- FP64 on the same batch
+    plan64, x64, y64, _ = setup("fp64")
+    steps64 = max(3, args.steps // 20)
+    secs64, _ = timed(lambda: step(plan64, x64, y64, sc), steps64, 3)
+    secs64 = max_over_ranks(secs64, world)
+    value64 = out_samples * steps64 / secs64 / 1e6
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timing
+    h_in = torch.tensor(batch["flat"], dtype=torch.float32).pin_memory()
+    h_out = torch.empty(batch["n_out"], dtype=torch.float32).pin_memory()
+    h_cls = torch.tensor(batch["cls"]).pin_memory()
+    d_cls = torch.empty_like(sc)
+
+    def e2e_step():
+        x32.copy_(h_in, non_blocking=True)
+        d_cls.copy_(h_cls, non_blocking=True)
+        step(plan32, x32, y32, d_cls)
+        h_out.copy_(y32, non_blocking=True)
+
+    e2e_steps = max(5, args.steps // 10)
+    secs_e2e, _ = timed(e2e_step, e2e_steps, 3)
+    secs_e2e = max_over_ranks(secs_e2e, world)
+    e2e_value = out_samples * e2e_steps / secs_e2e / 1e6
+
+    # ---- realised error against the FP64 oracle (stratified sample) and the CPU baseline
+    cpu = None
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        idx = oracle_sample(batch, n_per_class=12)
+        ref, cpu_s = run_oracle(batch, idx)
+        yh = y32.cpu().double().numpy()
+        yh64 = y64.cpu().numpy()
+        errs, errs64 = {}, {}
+        for b in idx:
+            P = int(batch["P"][b])
+            o0 = int(batch["out_off"][b])
+            r = ref[b][0]
+            rms = float(np.sqrt(np.mean(r ** 2)))
+            e32 = float(np.max(np.abs(yh[o0:o0 + S_FACTOR * P] - r)))
+            e64 = float(np.max(np.abs(yh64[o0:o0 + S_FACTOR * P] - r)))
+            errs.setdefault(P, []).append(e32 / rms)
+            errs64.setdefault(P, []).append(e64)
+        err = {"fp32_max_abs_over_rms": {str(k): max(v) for k, v in errs.items()},
+               "fp64_max_abs": {str(k): max(v) for k, v in errs64.items()},
+               "signals": len(idx)}
+        n_cpu_out = sum(S_FACTOR * int(batch["P"][b]) for b in idx)
+        cpu = {"value": n_cpu_out / cpu_s / 1e6, "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"{len(idx)} signals, 12 of each P class (6 trig, 6 smooth), FP64 direct "
+                         f"sum formula, {cpu_s:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "signals_per_gpu": N_SIGNALS, "M": 3,
+                       "P_choices": P_CHOICES, "T": "4P",
+                       "l2": "inputs larger than L2 (%.0f MB in, %.0f MB out per step)"
+                             % (4 * batch["n_in"] / 1e6, 4 * batch["n_out"] / 1e6),
+                       "parallelism": f"independent signals per GPU x{world}"},
+            "clocks": clocks,
+            "gpu_launches": (1 + n_cls) * args.steps,
+            "roofline": {"bound": "hbm", "achieved": k_achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": k_achieved / hbm, "traffic": None,
+                         "kernel": "mci_kernel<float, N=2048> (P=4096 tiles), timed alone",
+                         "bytes_per_launch": k_bytes, "ms_per_launch": k_ms,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "step_roofline": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                              "bytes_per_step": bytes_step},
+            "fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * secs64 / steps64,
+                     "speedup_fp32_over_fp64": value / value64},
+            "err_vs_oracle": err,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * batch["n_in"] + 4 * N_SIGNALS,
+                    "d2h_bytes_per_step": 4 * batch["n_out"]},
+            "cpu_baseline": cpu,
+            "plan": {"smem_bytes": info["smem_bytes"], "signals_per_cta": info["signals_per_cta"][:n_cls]},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
