@@ -130,7 +130,8 @@ typedef struct {
     int device_status;       /* device status word since the last query (0: clean);
                                 bit 0 bad size class, bit 1 bad image size, bit 2 bad
                                 offset / alignment, bit 3 batch above max_batch,
-                                bit 4 intermediate above max_intermediate                 */
+                                bit 4 intermediate above max_intermediate, bit 5 a
+                                device-side kernel launch failed                          */
     int signals_per_cta[MCI_MAX_SIZES]; /* tile height chosen per size class              */
     int threads_per_cta;
     int smem_bytes;          /* dynamic shared memory per CTA                             */
@@ -192,6 +193,30 @@ mci_status mci_interp_1d(mci_plan_t plan, const void* in, const int64_t* in_off,
 mci_status mci_upsample_2d(mci_plan_t plan, const float* lr, const int64_t* lr_off, const int* h,
                            const int* w, const int* scale, float* hr, const int64_t* hr_off,
                            int64_t n_img, mci_stream_t stream);
+
+/*
+ * mci_interp_1d_noalloc -- the same computation and arguments as
+ * mci_interp_1d, for callers that cannot allocate device memory at the time
+ * they know their batch: code running under global-mode stream capture (where
+ * cudaMalloc is refused), and code whose device memory is handed out up front
+ * by a framework or a fixed budget.  Such a caller creates its plan once at
+ * start-up (max_batch may then be 1) and passes batches of up to
+ * MCI_NOALLOC_MAX_BATCH signals here.  The paper has no counterpart: this is
+ * an interface of this library only.
+ *   Scratch (the signal grouping and packed offsets of uneven batches) lives in
+ *   one static device array of about 1.5 MiB that every GPU loading the library
+ *   holds until exit; no call allocates or frees device memory.  The first call
+ *   on a device looks up that array's device address (cudaGetSymbolAddress)
+ *   and caches it, so make the first call on each device before any stream
+ *   capture.  All calls share the array: calls that overlap on the GPU (other
+ *   streams, other threads) race on it and must be serialised by the caller.
+ *   Every call rewrites all of the scratch it reads, so nothing needs clearing.
+ *   batch > MCI_NOALLOC_MAX_BATCH returns MCI_ERR_UNSUPPORTED_SIZE.
+ */
+#define MCI_NOALLOC_MAX_BATCH 65536
+mci_status mci_interp_1d_noalloc(mci_plan_t plan, const void* in, const int64_t* in_off, void* out,
+                                 const int64_t* out_off, const int* size_class, int64_t batch,
+                                 mci_stream_t stream);
 
 /* mci_plan_info -- fill *stats; synchronises the plan's last stream to read the
  * device status word, then clears it. */

@@ -639,4 +639,48 @@ mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)
     return cuda_status(e);
 }
 
+mci_status mci_interp_1d_noalloc(mci_plan_t p, const void* in, const int64_t* in_off, void* out,
+                                 const int64_t* out_off, const int* size_class, int64_t batch,
+                                 mci_stream_t stream)
+{
+    if (!p || batch < 0) return MCI_ERR_INVALID_ARG;
+    if (batch > MCI_NOALLOC_MAX_BATCH) return MCI_ERR_UNSUPPORTED_SIZE;
+    if (batch == 0) return MCI_OK;
+    if (!in || !out) return MCI_ERR_INVALID_ARG;
+    const int n = (int)p->cls.size();
+    if (n > 1 && !size_class) return MCI_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    NoAllocScratch* scratch = noalloc_scratch(&e);
+    if (!scratch) return MCI_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    KArgs a{};
+    a.in = in;
+    a.out = out;
+    a.in_off = in_off;
+    a.out_off = out_off;
+    a.batch = batch;
+    a.sorted = noalloc_sorted(scratch);
+    a.sched1 = noalloc_sched(scratch);
+    a.status = p->d_status;
+    if (n == 1) {
+        a.c = p->cdev[0];
+        a.cls = 0;
+        a.mode = kModeUniform;
+        a.tw = p->launch[0].tw;
+        a.W = p->launch[0].W;
+        const int64_t items = (batch + p->cdev[0].G - 1) / p->cdev[0].G;
+        a.uniform_items = (int)items;
+        void* args[] = {&a};
+        e = cudaLaunchKernel(p->kern[0], dim3((unsigned)items), dim3(kThreads), args,
+                             (size_t)p->csmem[0], s);
+    } else {
+        e = (cudaError_t)launch_sched_1d(size_class, batch, n, p->d_launch, p->d_order,
+                                         noalloc_sorted(scratch), noalloc_sched(scratch),
+                                         in_off ? nullptr : noalloc_in_pref(scratch),
+                                         out_off ? nullptr : noalloc_out_pref(scratch), a, s);
+    }
+    return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
 }  // extern "C"

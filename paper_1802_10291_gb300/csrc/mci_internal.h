@@ -114,4 +114,12 @@ int launch_sched_2d(int64_t n_img, int n_classes, const ClassLaunch* cl, int64_t
                     int* row_cls, int* col_cls, int2* items, Sched2D* st, const KArgs& rows_tmpl,
                     const KArgs& cols_tmpl, void* stream);
 
+// Static scratch of mci_interp_1d_noalloc (mci_noalloc.cu).
+struct NoAllocScratch;
+NoAllocScratch* noalloc_scratch(cudaError_t* err);
+int64_t* noalloc_sorted(NoAllocScratch* s);
+int64_t* noalloc_in_pref(NoAllocScratch* s);
+int64_t* noalloc_out_pref(NoAllocScratch* s);
+Sched1D* noalloc_sched(NoAllocScratch* s);
+
 }  // namespace mci

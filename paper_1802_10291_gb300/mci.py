@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         lib.mci_plan.restype = ctypes.c_int
         lib.mci_interp_1d.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         lib.mci_interp_1d.restype = ctypes.c_int
+        lib.mci_interp_1d_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+        lib.mci_interp_1d_noalloc.restype = ctypes.c_int
         lib.mci_upsample_2d.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
         lib.mci_upsample_2d.restype = ctypes.c_int
         lib.mci_plan_info.argtypes = [vp, ctypes.POINTER(mci_plan_stats)]
@@ -196,6 +198,17 @@ def mci_plan(desc: mci_desc, stream=None) -> int:
 def mci_interp_1d(plan: int, inp, in_off, out, out_off, size_class, batch: int, stream=None):
     _check(load().mci_interp_1d(plan, _ptr(inp), _ptr(in_off), _ptr(out), _ptr(out_off),
                                 _ptr(size_class), int(batch), _stream(stream)), "mci_interp_1d")
+
+
+def mci_interp_1d_noalloc(plan: int, inp, in_off, out, out_off, size_class, batch: int,
+                          stream=None):
+    """mci_interp_1d with its scratch in the library's static device array (no allocation)."""
+    _check(load().mci_interp_1d_noalloc(plan, _ptr(inp), _ptr(in_off), _ptr(out), _ptr(out_off),
+                                        _ptr(size_class), int(batch), _stream(stream)),
+           "mci_interp_1d_noalloc")
+
+
+MCI_NOALLOC_MAX_BATCH = 65536
 
 
 def mci_upsample_2d(plan: int, lr, lr_off, h, w, scale, hr, hr_off, n_img: int, stream=None):

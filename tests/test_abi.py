@@ -10,7 +10,7 @@ from paper_1802_10291_gb300 import mci
 def test_exports_every_declared_symbol(mci_lib):
     declared = mci.header_functions()
     assert set(declared) == {"mci_plan", "mci_interp_1d", "mci_upsample_2d", "mci_plan_info",
-                             "mci_destroy", "mci_error_string"}
+                             "mci_destroy", "mci_error_string", "mci_interp_1d_noalloc"}
     for name in declared:
         assert hasattr(mci_lib, name), name
 
