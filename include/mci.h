@@ -164,7 +164,15 @@ mci_status mci_plan(mci_plan_t* plan, const mci_desc* desc, mci_stream_t stream)
  *              of bits in out_flags), output-major, out[o * T_c + j] = value at
  *              t_j = 2 pi j / T_c
  *   out_off    device int64 element offsets, or NULL: packed back to back
- *   size_class device int per signal (0 .. n_sizes-1), or NULL when n_sizes == 1
+ *   size_class int per signal (0 .. n_sizes-1), or NULL when n_sizes == 1.  In
+ *              DEVICE memory the batch is grouped by size class on the device and
+ *              each class's kernel is launched from there (stream-capturable;
+ *              class indices out of range set device_status bit 0).  In HOST
+ *              memory the call groups the batch on the host (reading the array
+ *              before it returns), uploads the grouping from pinned staging and
+ *              launches each class from the host on plan-owned streams forked
+ *              from and joined into `stream` -- the faster path; an index out of
+ *              range returns MCI_ERR_INVALID_ARG; not for stream capture.
  *   batch      number of signals, 0 .. max_batch
  * Offsets that are multiples of 4 elements (FP32) or 2 (FP64) take the
  * vectorised path; others work but run slower.

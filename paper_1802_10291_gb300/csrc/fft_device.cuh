@@ -178,20 +178,6 @@ __device__ __forceinline__ void dft(cpx<R>* v)
 // pass last).  Because the radix-3 pass comes last, every Ns before it is a
 // power of two, so all index arithmetic is shifts and masks.
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr int pick_radix(int rem, int E)
-{
-    return rem == 3 ? 3
-         : (rem % 16 == 0 && E % 16 == 0) ? 16
-         : (rem % 8 == 0 && E % 8 == 0) ? 8
-         : (rem % 4 == 0 && E % 4 == 0) ? 4
-         : 2;
-}
-
-__host__ __device__ constexpr int elems_per_thread(int n)
-{
-    return n % 3 == 0 ? (n >= 12 ? 12 : n) : (n >= 16 ? 16 : n);
-}
-
 __device__ __forceinline__ int ilog2(int x) { return 31 - __clz(x); }
 
 // Returns x through an opaque move, so index arithmetic derived from it is
@@ -210,35 +196,23 @@ __device__ __forceinline__ int opaque(int x)
 // kernel spill).
 __device__ __forceinline__ int ltid() { return opaque((int)threadIdx.x); }
 
-// Twiddle load that the compiler may not hoist out of the enclosing loops (the
-// tables are read-only; a volatile load keeps each pass's twiddles local to it).
-__device__ __forceinline__ cpx<float> ld_tw(const cpx<float>* p)
-{
-    float2 v;
-    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-    return {v.x, v.y};
-}
-__device__ __forceinline__ cpx<double> ld_tw(const cpx<double>* p)
-{
-    double2 v;
-    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
-    return {v.x, v.y};
-}
-
 // One Stockham pass of radix RAD over nfft length-N buffers (buffer f at
 // sm + base_of(f)); E elements per thread, groups of N/E threads per buffer.
-template <typename R, int E, int RAD, bool INV, typename BaseFn>
+// Butterfly j needs w^r, r < RAD, w = e^{-2 pi i (j mod NS) / (NS RAD)}: w is read
+// from this pass's shared-memory twiddle row stw (built at tile start), its
+// powers come from a product tree of depth <= 4.  With GIN the pass reads its
+// input from global memory (src_of(f), natural order, first pass only).
+template <typename R, int E, int RAD, bool INV, bool GIN, typename BaseFn, typename SrcFn>
 __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int N, int NS, int nfft, BaseFn base_of,
-                                              const cpx<R>* __restrict__ tw)
+                                              SrcFn src_of, const cpx<R>* stw)
 {
     constexpr int NB = E / RAD;
     const int TPF = N / E;
-    const int groups = blockDim.x / TPF;
     const int tix = ltid();
+    const int groups = blockDim.x / TPF;
     const int gi = tix / TPF;
     const int lt = tix - gi * TPF;
     const int stride = N / RAD;
-    const int twstep = 2 * (stride / NS);  // table holds e^{-2 pi i q / (2N)}
     const int lgNS = ilog2(NS);            // NS is a power of two
 #pragma unroll 1
     for (int f0 = 0; f0 < nfft; f0 += groups) {
@@ -247,15 +221,28 @@ __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int N, int NS, int nff
         cpx<R>* buf = sm + (active ? base_of(f) : 0);
         const int ltr = opaque(lt);
         cpx<R> v[NB * RAD];
+        cpx<R> w1[NB];
+        if (active && NS > 1) {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) w1[i] = stw[(ltr + i * TPF) & (NS - 1)];
+        }
         if (active) {
+            if constexpr (GIN) {
+                const cpx<R>* src = src_of(f);
 #pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                const int j = ltr + i * TPF;
+                for (int i = 0; i < NB; ++i)
 #pragma unroll
-                for (int r = 0; r < RAD; ++r) v[i * RAD + r] = buf[pad16(j + r * stride)];
+                    for (int r = 0; r < RAD; ++r) v[i * RAD + r] = src[ltr + i * TPF + r * stride];
+            } else {
+#pragma unroll
+                for (int i = 0; i < NB; ++i) {
+                    const int j = ltr + i * TPF;
+#pragma unroll
+                    for (int r = 0; r < RAD; ++r) v[i * RAD + r] = buf[pad16(j + r * stride)];
+                }
             }
         }
-        __syncthreads();
+        if constexpr (!GIN) __syncthreads();
         if (active) {
             const int lts = opaque(lt);
 #pragma unroll
@@ -263,11 +250,14 @@ __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int N, int NS, int nff
                 const int j = lts + i * TPF;
                 const int jm = j & (NS - 1);
                 if (NS > 1) {
+                    cpx<R> w[RAD];
+                    w[1] = w1[i];
 #pragma unroll
-                    for (int r = 1; r < RAD; ++r) {
-                        const cpx<R> w = ld_tw(tw + jm * r * twstep);
-                        v[i * RAD + r] = INV ? cmulc(v[i * RAD + r], w) : cmul(v[i * RAD + r], w);
-                    }
+                    for (int r = 2; r < RAD; ++r)
+                        w[r] = (r & 1) ? cmul(w[r - 1], w[1]) : cmul(w[r / 2], w[r / 2]);
+#pragma unroll
+                    for (int r = 1; r < RAD; ++r)
+                        v[i * RAD + r] = INV ? cmulc(v[i * RAD + r], w[r]) : cmul(v[i * RAD + r], w[r]);
                 }
                 dft<RAD, INV>(&v[i * RAD]);
                 const int d = ((j >> lgNS) << lgNS) * RAD + jm;
@@ -279,25 +269,64 @@ __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int N, int NS, int nff
     }
 }
 
-// Compile-time radix sequence of a length-N transform with E elements per thread:
-// the largest radix dividing E while it divides the rest, then the remaining
-// power-of-two radix, then radix 3 last where N has that factor.
-template <typename R, int N, int E, int NS, bool INV, typename BaseFn>
-__device__ __forceinline__ void fft_passes_ct(cpx<R>* sm, int nfft, BaseFn base_of,
-                                              const cpx<R>* __restrict__ tw)
+struct NoSrc {
+    template <typename T>
+    __device__ __forceinline__ const T* operator()(int) const { return nullptr; }
+};
+
+// Compile-time radix sequence of a length-N transform with E elements per thread
+// (pick_radix); stw is the shared-memory twiddle table (smem_twiddle_offset).
+template <typename R, int N, int E, int NS, bool INV, bool GIN, typename BaseFn, typename SrcFn>
+__device__ __forceinline__ void fft_passes_ct(cpx<R>* sm, int nfft, BaseFn base_of, SrcFn src_of,
+                                              const cpx<R>* stw)
 {
     if constexpr (NS < N) {
         constexpr int RAD = pick_radix(N / NS, E);
-        fft_pass_many<R, E, RAD, INV>(sm, N, NS, nfft, base_of, tw);
-        fft_passes_ct<R, N, E, NS * RAD, INV>(sm, nfft, base_of, tw);
+        fft_pass_many<R, E, RAD, INV, GIN && NS == 1>(sm, N, NS, nfft, base_of, src_of,
+                                                        stw + smem_twiddle_offset(N, NS));
+        fft_passes_ct<R, N, E, NS * RAD, INV, GIN>(sm, nfft, base_of, src_of, stw);
     }
 }
 
-template <typename R, int N, bool INV, typename BaseFn>
-__device__ __forceinline__ void fft_many_ct(cpx<R>* sm, int nfft, BaseFn base_of,
-                                            const cpx<R>* __restrict__ tw)
+// nfft transforms of length N held in shared memory (GIN: read from global memory).
+template <typename R, int N, bool INV, bool GIN = false, typename BaseFn, typename SrcFn = NoSrc>
+__device__ __forceinline__ void fft_many_ct(cpx<R>* sm, int nfft, BaseFn base_of, const cpx<R>* stw,
+                                            SrcFn src_of = SrcFn())
 {
-    fft_passes_ct<R, N, elems_per_thread(N), 1, INV>(sm, nfft, base_of, tw);
+    fft_passes_ct<R, N, elems_per_thread(N), 1, INV, GIN>(sm, nfft, base_of, src_of, stw);
+}
+
+// e^{-2 pi i num / den}
+template <typename R>
+__device__ __forceinline__ cpx<R> cis_neg(int num, int den);
+template <>
+__device__ __forceinline__ cpx<float> cis_neg<float>(int num, int den)
+{
+    float s, c;
+    sincospif(2.0f * (float)num / (float)den, &s, &c);
+    return {c, -s};
+}
+template <>
+__device__ __forceinline__ cpx<double> cis_neg<double>(int num, int den)
+{
+    double s, c;
+    sincospi(2.0 * (double)num / (double)den, &s, &c);
+    return {c, -s};
+}
+
+// Fill the shared-memory twiddle table of a length-N transform (all threads call;
+// the caller's barrier follows).
+template <typename R, int N, int E, int NS>
+__device__ __forceinline__ void fill_twiddles_ct(cpx<R>* stw)
+{
+    if constexpr (NS < N) {
+        constexpr int RAD = pick_radix(N / NS, E);
+        if constexpr (NS > 1) {
+            for (int jm = ltid(); jm < NS; jm += blockDim.x)
+                stw[smem_twiddle_offset(N, NS) + jm] = cis_neg<R>(jm, NS * RAD);
+        }
+        fill_twiddles_ct<R, N, E, NS * RAD>(stw);
+    }
 }
 
 }  // namespace mci

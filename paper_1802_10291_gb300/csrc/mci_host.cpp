@@ -190,10 +190,9 @@ struct mci_plan_s {
     size_t elem = 4;                  // sizeof(real)
     int64_t max_items = 0;            // 2-D work-list capacity
     // device memory
-    void* d_tables = nullptr;         // launch info | order | tw | W
+    void* d_tables = nullptr;         // launch info | order | W
     ClassLaunch* d_launch = nullptr;
     int* d_order = nullptr;
-    void* d_tw = nullptr;
     void* d_W = nullptr;
     int64_t table_bytes = 0;
     void* d_work = nullptr;           // 1-D and 2-D workspace
@@ -212,6 +211,15 @@ struct mci_plan_s {
     int2* d_items = nullptr;
     Sched2D* d_sched2 = nullptr;
     cudaStream_t last_stream = nullptr;
+    // host-grouped uneven batches: per-class streams, fork/join events, pinned staging
+    std::vector<cudaStream_t> cstreams;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
+    char* h_stage[2] = {nullptr, nullptr};   // mirrors the device block d_sorted .. d_sched1
+    cudaEvent_t ev_stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    size_t off_in_pref = 0, off_out_pref = 0, off_sched1 = 0;  // offsets inside the block
+    int stage_cur = 0;
 };
 
 namespace {
@@ -279,7 +287,7 @@ void push_cpx(std::vector<R>& v, cd z)
 }
 
 template <typename R>
-mci_status build_tables(mci_plan_s* p, std::vector<R>& tw, std::vector<R>& W)
+mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
 {
     const mci_desc& d = p->desc;
     const int M = d.M, Min = p->M_in, nout = p->n_out;
@@ -301,9 +309,8 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& tw, std::vector<R>& W)
         p->n_singular += inv.n_singular;
         p->max_cond = std::max(p->max_cond, inv.max_cond);
         ClassDev& cd_ = p->cdev[c];
-        cd_.tw_off = (int64_t)(tw.size() / 2);
+        if ((W.size() / 2) % 2) push_cpx(W, cd(0.0));  // 16-byte aligned class region
         cd_.w_off = (int64_t)(W.size() / 2);
-        for (int q = 0; q < P; ++q) push_cpx(tw, cis_frac(-q, P));
         // W_r[m][q] = (1/P) sum_j Q_r[m][j] o(n_j) e^{2 pi i n_j u / T}, n_j = N1 + r + j P
         auto Wfull = [&](int r, int m, int q) {
             const int o = ops[q / s], u = q % s;
@@ -339,6 +346,71 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& tw, std::vector<R>& W)
 
 }  // namespace
 
+// Uneven batch whose size classes are in host memory: stable grouping on the host
+// into a pinned staging block (two blocks alternate; a block is reused only after
+// its previous upload has completed), one upload, then every non-empty class is
+// launched from the host with its exact grid on its own stream, forked from and
+// joined back into the caller's stream.
+static mci_status interp_1d_host_grouped(mci_plan_t p, KArgs a, const int* size_class, int64_t batch,
+                                         cudaStream_t s)
+{
+    const int n = (int)p->cls.size();
+    char* blk = p->h_stage[p->stage_cur];
+    cudaEvent_t ev = p->ev_stage[p->stage_cur];
+    if (cudaEventSynchronize(ev) != cudaSuccess) return MCI_ERR_CUDA;
+    int64_t* sorted = (int64_t*)blk;
+    int64_t* in_pref = (int64_t*)(blk + p->off_in_pref);
+    int64_t* out_pref = (int64_t*)(blk + p->off_out_pref);
+    Sched1D* st = (Sched1D*)(blk + p->off_sched1);
+    std::vector<int64_t> cnt(n, 0), pos(n, 0);
+    for (int64_t b = 0; b < batch; ++b) {
+        const int c = size_class[b];
+        if (c < 0 || c >= n) return MCI_ERR_INVALID_ARG;
+        ++cnt[c];
+    }
+    int64_t acc = 0;
+    for (int oi = 0; oi < n; ++oi) {
+        const int c = p->order[oi];
+        pos[c] = acc;
+        st->start[c] = (int)acc;
+        st->count[c] = (int)cnt[c];
+        acc += cnt[c];
+    }
+    int64_t pin = 0, pout = 0;
+    for (int64_t b = 0; b < batch; ++b) {
+        const int c = size_class[b];
+        sorted[pos[c]++] = b;
+        in_pref[b] = pin;
+        out_pref[b] = pout;
+        pin += (int64_t)p->cdev[c].M_in * p->cdev[c].P;
+        pout += (int64_t)p->cdev[c].n_out * p->cdev[c].T;
+    }
+    cudaError_t e = cudaMemcpyAsync(p->d_sorted, blk, p->stage_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, s);
+    p->stage_cur ^= 1;
+    if (!a.in_off) a.in_off = p->d_in_pref;
+    if (!a.out_off) a.out_off = p->d_out_pref;
+    a.mode = kModeSorted;
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
+    for (int oi = 0; oi < n && e == cudaSuccess; ++oi) {
+        const int c = p->order[oi];
+        if (cnt[c] == 0) continue;
+        const int64_t grid = (cnt[c] + p->cdev[c].G - 1) / p->cdev[c].G;
+        KArgs ac = a;
+        ac.c = p->cdev[c];
+        ac.cls = c;
+        ac.W = p->launch[c].W;
+        void* args[] = {&ac};
+        e = cudaStreamWaitEvent(p->cstreams[c], p->ev_fork, 0);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(p->kern[c], dim3((unsigned)grid), dim3(kThreads), args,
+                                 (size_t)p->csmem[c], p->cstreams[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_join[c], p->cstreams[c]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[c], 0);
+    }
+    return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
 extern "C" {
 
 const char* mci_error_string(mci_status s)
@@ -360,6 +432,15 @@ mci_status mci_destroy(mci_plan_t p)
 {
     if (!p) return MCI_OK;
     cudaDeviceSynchronize();
+    for (cudaStream_t cs : p->cstreams)
+        if (cs) cudaStreamDestroy(cs);
+    for (cudaEvent_t ev : p->ev_join)
+        if (ev) cudaEventDestroy(ev);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    for (int i = 0; i < 2; ++i) {
+        if (p->ev_stage[i]) cudaEventDestroy(p->ev_stage[i]);
+        if (p->h_stage[i]) cudaFreeHost(p->h_stage[i]);
+    }
     if (p->d_tables) cudaFree(p->d_tables);
     if (p->d_work) cudaFree(p->d_work);
     delete p;
@@ -416,7 +497,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         cd_.Q = hc.s * p->n_out;
         cd_.QM = std::max(cd_.M_in, cd_.Q);
         cd_.npad = padded_len(hc.N);
-        const int per = cd_.QM * cd_.npad * csz;
+        const int per = cd_.QM * cd_.npad * csz + smem_twiddle_count(hc.N) * csz;
         if (per > smem_cap) {
             delete p;
             return MCI_ERR_UNSUPPORTED_SIZE;
@@ -428,8 +509,13 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     for (int c = 0; c < n; ++c) {
         ClassDev& cd_ = p->cdev[c];
         const int per = cd_.QM * cd_.npad * csz;
-        cd_.G = std::max(1, std::min(kMaxTile, budget / per));
-        p->csmem[c] = cd_.G * per;
+        const int twb = smem_twiddle_count(cd_.N) * csz;   // FFT twiddles after the buffers
+        cd_.G = std::max(1, std::min(kMaxTile, (budget - twb) / per));
+        p->csmem[c] = cd_.G * per + twb;
+        if (p->csmem[c] > smem_cap) {
+            delete p;
+            return MCI_ERR_UNSUPPORTED_SIZE;
+        }
         p->smem = std::max(p->smem, p->csmem[c]);
     }
     p->order.resize(n);
@@ -438,20 +524,18 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
                      [&](int a, int b) { return p->cls[a].P > p->cls[b].P; });
 
     // FP64 tables
-    std::vector<float> tw32, W32;
-    std::vector<double> tw64, W64;
-    st = d.precision == MCI_FP64 ? build_tables<double>(p, tw64, W64) : build_tables<float>(p, tw32, W32);
+    std::vector<float> W32;
+    std::vector<double> W64;
+    st = d.precision == MCI_FP64 ? build_tables<double>(p, W64) : build_tables<float>(p, W32);
     if (st != MCI_OK) {
         delete p;
         return st;
     }
-    const void* tw_src = d.precision == MCI_FP64 ? (const void*)tw64.data() : (const void*)tw32.data();
     const void* W_src = d.precision == MCI_FP64 ? (const void*)W64.data() : (const void*)W32.data();
-    const size_t tw_bytes = (d.precision == MCI_FP64 ? tw64.size() : tw32.size()) * p->elem;
     const size_t W_bytes = (d.precision == MCI_FP64 ? W64.size() : W32.size()) * p->elem;
     const size_t launch_bytes = align_up(sizeof(ClassLaunch) * n, 256);
     const size_t order_bytes = align_up(sizeof(int) * n, 256);
-    const size_t total = launch_bytes + order_bytes + align_up(tw_bytes, 256) + align_up(W_bytes, 256);
+    const size_t total = launch_bytes + order_bytes + align_up(W_bytes, 256);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMalloc(&p->d_tables, total);
     if (e != cudaSuccess) {
@@ -462,29 +546,32 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     char* base = (char*)p->d_tables;
     p->d_launch = (ClassLaunch*)base;
     p->d_order = (int*)(base + launch_bytes);
-    p->d_tw = base + launch_bytes + order_bytes;
-    p->d_W = base + launch_bytes + order_bytes + align_up(tw_bytes, 256);
+    p->d_W = base + launch_bytes + order_bytes;
     p->launch.resize(n);
     p->kern.resize(n);
     p->kern_cols.resize(n);
     for (int c = 0; c < n; ++c) {
         ClassLaunch& L = p->launch[c];
         L.c = p->cdev[c];
-        L.tw = (const char*)p->d_tw + p->cdev[c].tw_off * 2 * p->elem;
         L.W = (const char*)p->d_W + p->cdev[c].w_off * 2 * p->elem;
         L.prec = d.precision;
         L.smem = p->csmem[c];
         p->kern[c] = kernel_lookup(d.precision, false, p->cdev[c].N);
         p->kern_cols[c] = d.precision == MCI_FP32 ? kernel_lookup(d.precision, true, p->cdev[c].N) : nullptr;
         if (!p->kern[c]) e = cudaErrorInvalidDeviceFunction;
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(p->kern[c], cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
-        if (e == cudaSuccess && p->kern_cols[c])
-            e = cudaFuncSetAttribute(p->kern_cols[c], cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+        // Dynamic shared memory limit, and the largest shared-memory carveout: launches from
+        // the device-side scheduler do not get the carveout sized to their request, and
+        // without it fewer CTAs fit on an SM.
+        for (const void* k : {p->kern[c], p->kern_cols[c]}) {
+            if (!k || e != cudaSuccess) continue;
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_launch, p->launch.data(), sizeof(ClassLaunch) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_order, p->order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_tw, tw_src, tw_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_W, W_src, W_bytes, cudaMemcpyHostToDevice, s);
 
     // workspace
@@ -535,6 +622,24 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         p->d_items = (int2*)(w + o_it);
         p->d_sched2 = (Sched2D*)(w + o_s2);
     }
+    // host-grouped path: one stream per class, fork/join events, two pinned staging blocks
+    p->stage_bytes = o_s1 + sizeof(Sched1D) - o_sorted;
+    p->off_in_pref = o_inp - o_sorted;
+    p->off_out_pref = o_outp - o_sorted;
+    p->off_sched1 = o_s1 - o_sorted;
+    if (n > 1 && e == cudaSuccess) {
+        p->cstreams.assign(n, nullptr);
+        p->ev_join.assign(n, nullptr);
+        for (int c = 0; c < n && e == cudaSuccess; ++c) {
+            e = cudaStreamCreateWithFlags(&p->cstreams[c], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[c], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaHostAlloc((void**)&p->h_stage[i], p->stage_bytes, cudaHostAllocDefault);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_stage[i], cudaEventDisableTiming);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int) * 4, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -572,7 +677,6 @@ mci_status mci_interp_1d(mci_plan_t p, const void* in, const int64_t* in_off, vo
         a.c = p->cdev[0];
         a.cls = 0;
         a.mode = kModeUniform;
-        a.tw = p->launch[0].tw;
         a.W = p->launch[0].W;
         const int64_t items = (batch + p->cdev[0].G - 1) / p->cdev[0].G;
         if (items > 0x7fffffff) return MCI_ERR_UNSUPPORTED_SIZE;
@@ -581,6 +685,13 @@ mci_status mci_interp_1d(mci_plan_t p, const void* in, const int64_t* in_off, vo
         e = cudaLaunchKernel(p->kern[0], dim3((unsigned)items), dim3(kThreads), args,
                              (size_t)p->csmem[0], s);
     } else {
+        cudaPointerAttributes attr{};
+        if (cudaPointerGetAttributes(&attr, size_class) != cudaSuccess) {
+            cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+            attr.type = cudaMemoryTypeUnregistered;
+        }
+        const bool on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+        if (!on_device) return interp_1d_host_grouped(p, a, size_class, batch, s);
         e = (cudaError_t)launch_sched_1d(size_class, batch, n, p->d_launch, p->d_order, p->d_sorted,
                                          p->d_sched1, in_off ? nullptr : p->d_in_pref,
                                          out_off ? nullptr : p->d_out_pref, a, s);
@@ -667,7 +778,6 @@ mci_status mci_interp_1d_noalloc(mci_plan_t p, const void* in, const int64_t* in
         a.c = p->cdev[0];
         a.cls = 0;
         a.mode = kModeUniform;
-        a.tw = p->launch[0].tw;
         a.W = p->launch[0].W;
         const int64_t items = (batch + p->cdev[0].G - 1) / p->cdev[0].G;
         a.uniform_items = (int)items;

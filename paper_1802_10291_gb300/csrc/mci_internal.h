@@ -4,7 +4,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/mci.h"
+#include "mci.h"
 
 #ifdef __CUDACC__
 #define MCI_HD __host__ __device__
@@ -24,6 +24,37 @@ constexpr int kSmemBudget = 64 * 1024;  // preferred dynamic shared memory per C
 MCI_HD constexpr int pad16(int e) { return e + 2 * (e >> 5); }
 MCI_HD constexpr int padded_len(int n) { return ((pad16(n) + 1) / 2) * 2; }
 
+// Radix plan of a length-n FFT, shared by the host (twiddle tables) and the
+// kernels: E elements per thread; radix 16/8/4/2 on the power-of-two part and
+// one radix-3 pass last where n has a factor 3.
+MCI_HD constexpr int elems_per_thread(int n)
+{
+    return n % 3 == 0 ? (n >= 12 ? 12 : n) : (n >= 16 ? 16 : n);
+}
+MCI_HD constexpr int pick_radix(int rem, int E)
+{
+    return rem == 3 ? 3
+         : (rem % 16 == 0 && E % 16 == 0) ? 16
+         : (rem % 8 == 0 && E % 8 == 0) ? 8
+         : (rem % 4 == 0 && E % 4 == 0) ? 4
+         : 2;
+}
+// Shared-memory twiddles of a length-n FFT: for every pass with stride NS > 1 the
+// NS values w^{jm} = e^{-2 pi i jm / (NS RAD)}, jm < NS, one pass after the other.
+// smem_twiddle_offset(n, NS) is the first entry of the pass that starts at NS;
+// smem_twiddle_count(n) the total.
+MCI_HD constexpr int smem_twiddle_offset(int n, int NS)
+{
+    int off = 0, ns = 1;
+    while (ns < NS) {
+        const int rad = pick_radix(n / ns, elems_per_thread(n));
+        if (ns > 1) off += ns;
+        ns *= rad;
+    }
+    return off;
+}
+MCI_HD constexpr int smem_twiddle_count(int n) { return smem_twiddle_offset(n, n); }
+
 // One size class as the kernels see it.
 struct ClassDev {
     int P;       // samples per channel
@@ -36,7 +67,6 @@ struct ClassDev {
     int G;       // signals per tile
     int n_out;   // outputs per signal
     int npad;    // padded FFT buffer length (complex elements)
-    int64_t tw_off;  // offset (complex elements) of this class's twiddles e^{-2 pi i q/P}, q < P
     int64_t w_off;   // offset of this class's bin weights W[k][m][q], k = 0..N
 };
 
@@ -49,7 +79,6 @@ struct Sched1D {
 // What the device-side scheduler needs to launch one size class.
 struct ClassLaunch {
     ClassDev c;
-    const void* tw;
     const void* W;
     int prec;
     int smem;
@@ -82,7 +111,6 @@ struct KArgs {
     int mode;                // KernelMode
     const void* in;          // 1-D: samples; rows: LR images; cols: intermediate
     void* out;               // 1-D: outputs; rows: intermediate; cols: HR images
-    const void* tw;          // this class's twiddles (cpx<R>)
     const void* W;           // this class's bin weights (cpx<R>)
     // 1-D
     const int64_t* in_off;   // per signal, or NULL (packed)

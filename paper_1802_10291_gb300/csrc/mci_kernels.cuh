@@ -14,7 +14,6 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
     __shared__ int64_t s_out[kMaxTile];
     __shared__ int s_cnt;
     const ClassDev& c = a.c;
-    const cpx<R>* tw = static_cast<const cpx<R>*>(a.tw);
     const cpx<R>* W = static_cast<const cpx<R>*>(a.W);
     const int G = c.G;
     if constexpr (COLS) {
@@ -25,7 +24,7 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
         const int cnt = (int)min((int64_t)G, ld - c0);
         load_cols<R>(sm, c, static_cast<const R*>(a.in), a.inter_off[i] + c0, ld, cnt);
         __syncthreads();
-        compute_tile<R, N>(sm, c, cnt, tw, W);
+        compute_tile<R, N>(sm, c, cnt, W);
         store_cols<R>(sm, c, static_cast<R*>(a.out), a.img_out_off[i] + c0, ld, cnt);
         __syncthreads();
     } else {
@@ -59,9 +58,19 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
             }
         }
         __syncthreads();
-        load_contig<R>(sm, c, static_cast<const R*>(a.in), s_in, cnt);
-        __syncthreads();
-        compute_tile<R, N>(sm, c, cnt, tw, W);
+        // signals whose complex pairs are 8-byte aligned are read by the first FFT pass
+        // directly; others are staged in shared memory first
+        bool direct = (c.P % 2) == 0;
+        for (int g = 0; g < cnt; ++g)
+            direct = direct && ((reinterpret_cast<uintptr_t>(static_cast<const R*>(a.in) + s_in[g]) &
+                                 (2 * sizeof(R) - 1)) == 0);
+        if (direct) {
+            compute_tile<R, N>(sm, c, cnt, W, static_cast<const R*>(a.in), s_in);
+        } else {
+            load_contig<R>(sm, c, static_cast<const R*>(a.in), s_in, cnt);
+            __syncthreads();
+            compute_tile<R, N>(sm, c, cnt, W);
+        }
         store_contig<R>(sm, c, static_cast<R*>(a.out), s_out, cnt);
         __syncthreads();
     }
@@ -72,7 +81,7 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
 // spills.)  Launches size their grid to the class's tile count, from the host
 // for uniform batches, from the device-side scheduler otherwise.
 template <typename R, int N, bool COLS>
-__global__ void __launch_bounds__(kThreads, 2) mci_kernel(const KArgs a)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2) mci_kernel(const KArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);

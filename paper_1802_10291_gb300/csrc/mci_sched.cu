@@ -122,7 +122,6 @@ sched_1d_kernel(const int* __restrict__ size_class, int64_t batch, int n_classes
             KArgs a = tmpl;
             a.c = cl[c].c;
             a.cls = c;
-            a.tw = cl[c].tw;
             a.W = cl[c].W;
             a.mode = kModeSorted;
             if (!a.in_off) a.in_off = in_pref;
@@ -252,7 +251,6 @@ sched_2d_kernel(int64_t n_img, int n_classes, const ClassLaunch* __restrict__ cl
             KArgs a = tmpl;
             a.c = cl[c].c;
             a.cls = c;
-            a.tw = cl[c].tw;
             a.W = cl[c].W;
             a.mode = kModeRows;
             launch_class(cl[c], false, rcnt[c], a, tmpl.status);
@@ -270,7 +268,6 @@ __global__ void dispatch_cols_kernel(int n_classes, const ClassLaunch* __restric
         KArgs a = tmpl;
         a.c = cl[c].c;
         a.cls = c;
-        a.tw = cl[c].tw;
         a.W = cl[c].W;
         a.mode = kModeCols;
         launch_class(cl[c], true, n, a, tmpl.status);

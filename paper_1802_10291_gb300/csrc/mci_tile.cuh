@@ -21,9 +21,21 @@
 
 namespace mci {
 
+// Two consecutive weights (q, q + 1) in one 16-byte load where the type allows.
+__device__ __forceinline__ void ld_w2(const cpx<float>* p, cpx<float>& a, cpx<float>& b)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    a = {v.x, v.y};
+    b = {v.z, v.w};
+}
+__device__ __forceinline__ void ld_w2(const cpx<double>* p, cpx<double>& a, cpx<double>& b)
+{
+    a = p[0];
+    b = p[1];
+}
+
 template <typename R>
 __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int gcount,
-                                          const cpx<R>* __restrict__ tw,
                                           const cpx<R>* __restrict__ W)
 {
     const int npad = c.npad, QM = c.QM, Min = c.M_in, Q = c.Q, N = c.N;
@@ -34,7 +46,7 @@ __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int 
         const int k = it / gcount;
         const int kk = (N - k) % N;  // mirror bin (k = 0 pairs with bin N == 0 of Z)
         cpx<R>* base = sm + g * QM * npad;
-        const cpx<R> w = tw[k];      // e^{-2 pi i k / P}
+        const cpx<R> w = cis_neg<R>(k, c.P);  // e^{-2 pi i k / P}
         cpx<R> Xa[MCI_MAX_CHANNELS], Xb[MCI_MAX_CHANNELS];
 #pragma unroll
         for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
@@ -56,7 +68,35 @@ __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int 
         }
         const cpx<R>* Wa = W + (int64_t)k * Min * Q;
         const cpx<R>* Wb = W + (int64_t)(N - k) * Min * Q;
-        for (int q = 0; q < Q; ++q) {
+        // pack: Z'[k] = A + iC, Z'[N-k] = conj(A) + i conj(C),
+        // A = Y[k] + conj Y[N-k], C = e^{2 pi i k / P} (Y[k] - conj Y[N-k])
+        auto emit = [&](int q, cpx<R> ya, cpx<R> yb) {
+            const cpx<R> A = ya + conjc(yb);
+            const cpx<R> C = cmulc(ya - conjc(yb), w);
+            base[q * npad + pad16(k)] = mk<R>(A.x - C.y, A.y + C.x);
+            if (k != 0 && k != NH) base[q * npad + pad16(kk)] = mk<R>(A.x + C.y, C.x - A.y);
+        };
+        int q = 0;
+        if ((Q & 1) == 0) {
+            for (; q < Q; q += 2) {
+                cpx<R> ya0 = mk<R>(0, 0), yb0 = mk<R>(0, 0), ya1 = mk<R>(0, 0), yb1 = mk<R>(0, 0);
+#pragma unroll
+                for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
+                    if (m < Min) {
+                        cpx<R> wa0, wa1, wb0, wb1;
+                        ld_w2(Wa + m * Q + q, wa0, wa1);
+                        ld_w2(Wb + m * Q + q, wb0, wb1);
+                        ya0 = ya0 + cmul(Xa[m], wa0);
+                        ya1 = ya1 + cmul(Xa[m], wa1);
+                        yb0 = yb0 + cmul(Xb[m], wb0);
+                        yb1 = yb1 + cmul(Xb[m], wb1);
+                    }
+                }
+                emit(q, ya0, yb0);
+                emit(q + 1, ya1, yb1);
+            }
+        }
+        for (; q < Q; ++q) {
             cpx<R> ya = mk<R>(0, 0), yb = mk<R>(0, 0);
 #pragma unroll
             for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
@@ -65,12 +105,7 @@ __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int 
                     yb = yb + cmul(Xb[m], Wb[m * Q + q]);
                 }
             }
-            // pack: Z'[k] = A + iC, Z'[N-k] = conj(A) + i conj(C),
-            // A = Y[k] + conj Y[N-k], C = e^{2 pi i k / P} (Y[k] - conj Y[N-k])
-            const cpx<R> A = ya + conjc(yb);
-            const cpx<R> C = cmulc(ya - conjc(yb), w);
-            base[q * npad + pad16(k)] = mk<R>(A.x - C.y, A.y + C.x);
-            if (k != 0 && k != NH) base[q * npad + pad16(kk)] = mk<R>(A.x + C.y, C.x - A.y);
+            emit(q, ya, yb);
         }
     }
 }
@@ -85,44 +120,76 @@ struct SlotBase {
     }
 };
 
+// Channel f % M_in of tile signal f / M_in, read in place from global memory as
+// N complex values (even sample = real part).
+template <typename R>
+struct SrcContig {
+    const R* in;
+    const int64_t* off;
+    int Min, P;
+    __device__ __forceinline__ const cpx<R>* operator()(int f) const
+    {
+        const int g = f / Min;
+        return reinterpret_cast<const cpx<R>*>(in + off[g] + (int64_t)(f - g * Min) * P);
+    }
+};
+
+// gin != nullptr: the tile's signals are read by the first forward pass directly
+// from gin + s_in[g] (8-byte aligned); otherwise they are already in shared memory.
+// The FFT twiddles live after the tile's buffers (smem_twiddle_offset); they are
+// filled here, before the first pass, which needs none and ends with a barrier.
 template <typename R, int N>
 __device__ __forceinline__ void compute_tile(cpx<R>* sm, const ClassDev& c, int gcount,
-                                             const cpx<R>* __restrict__ tw,
-                                             const cpx<R>* __restrict__ W)
+                                             const cpx<R>* __restrict__ W, const R* gin = nullptr,
+                                             const int64_t* s_in = nullptr)
 {
-    fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad}, tw);
-    combine_tile<R>(sm, c, gcount, tw, W);
+    cpx<R>* stw = sm + c.G * c.QM * c.npad;
+    fill_twiddles_ct<R, N, elems_per_thread(N), 1>(stw);
+    if (gin)
+        fft_many_ct<R, N, false, true>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad}, stw,
+                                       SrcContig<R>{gin, s_in, c.M_in, c.P});
+    else
+        fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad}, stw);
+    combine_tile<R>(sm, c, gcount, W);
     __syncthreads();
-    fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.QM, c.npad}, tw);
+    fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.QM, c.npad}, stw);
 }
 
 // ---------------------------------------------------------------------------
 // loads and stores
 // ---------------------------------------------------------------------------
 
-// Contiguous signals: signal g's M_in x P samples start at in + off[g].
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// Contiguous signals: signal g's M_in x P samples start at in + off[g].  Aligned
+// signals are copied with asynchronous 16-byte copies (all in flight at once);
+// the caller's barrier follows.
 template <typename R>
 __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const R* __restrict__ in,
                                             const int64_t* off, int gcount)
 {
     const int P = c.P, Min = c.M_in, npad = c.npad, QM = c.QM;
     const int per = Min * P;
-    constexpr int VW = sizeof(R) == 4 ? 4 : 2;  // reals per 16-byte vector
+    constexpr int VW = sizeof(R) == 4 ? 4 : 2;  // reals per 16-byte copy
+    bool async = false;
     for (int g = 0; g < gcount; ++g) {
         const R* src = in + off[g];
         cpx<R>* dst = sm + g * QM * npad;
         const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (P % VW == 0);
         if (vec) {
+            async = true;
             for (int t = ltid(); t < per / VW; t += blockDim.x) {
                 const int i = t * VW;
                 const int m = i / P, p = (i - m * P) >> 1;
-                if constexpr (sizeof(R) == 4) {
-                    const float4 v = __ldg(reinterpret_cast<const float4*>(src) + t);
-                    *reinterpret_cast<float4*>(&dst[m * npad + pad16(p)]) = v;
-                } else {
-                    const double2 v = __ldg(reinterpret_cast<const double2*>(src) + t);
-                    *reinterpret_cast<double2*>(&dst[m * npad + pad16(p)]) = v;
-                }
+                cp_async16(&dst[m * npad + pad16(p)], src + i);
             }
         } else {
             for (int i = ltid(); i < per; i += blockDim.x) {
@@ -132,6 +199,7 @@ __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const
             }
         }
     }
+    if (async) cp_async_wait_all();
 }
 
 // Contiguous outputs: output o of signal g at out + off[g] + o * T, T = s P samples;
@@ -151,13 +219,16 @@ __device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c
                 const int i0 = t * 4;
                 const int o = i0 / T;
                 const int x0 = i0 - o * T;
+                int l2 = x0 / s, u = x0 - l2 * s;   // sample x = s * l2 + u
                 R v[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int x = x0 + e;
-                    const int l2 = x / s, u = x - l2 * s;
                     const cpx<R> z = srcs[(o * s + u) * npad + pad16(l2 >> 1)];
                     v[e] = (l2 & 1) ? z.y : z.x;
+                    if (++u == s) {
+                        u = 0;
+                        ++l2;
+                    }
                 }
                 if constexpr (sizeof(R) == 4) {
                     reinterpret_cast<float4*>(dst)[t] = make_float4(v[0], v[1], v[2], v[3]);

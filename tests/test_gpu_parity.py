@@ -136,8 +136,10 @@ def test_fd_channels(cuda_device, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("packed", [True, False])
-def test_uneven_batch(cuda_device, prec, packed):
-    """Signals of several sizes in one call; device-side grouping and per-class launches."""
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_uneven_batch(cuda_device, prec, packed, where):
+    """Signals of several sizes in one call; size classes in device memory (grouped and
+    launched on the device) or in host memory (grouped and launched from the host)."""
     systems = [F, H, D1]
     Ps = [256, 64, 512, 24]
     rng = S.rng_for(1, 12)
@@ -157,7 +159,8 @@ def test_uneven_batch(cuda_device, prec, packed):
         flat[in_off[b]:in_off[b] + in_len[b]] = gs[b].ravel()
     x = torch.tensor(flat, dtype=DT[prec], device="cuda")
     y = torch.full((int(out_off[-1] + out_len[-1] + pad),), float("nan"), dtype=DT[prec], device="cuda")
-    sc = torch.tensor(cls, dtype=torch.int32, device="cuda")
+    sc = torch.tensor(cls, dtype=torch.int32, device="cuda") if where == "device" else \
+        np.ascontiguousarray(cls, dtype=np.int32)
     io = None if packed else torch.tensor(in_off, dtype=torch.int64, device="cuda")
     oo = None if packed else torch.tensor(out_off, dtype=torch.int64, device="cuda")
     mci.mci_interp_1d(plan.handle, x, io, y, oo, sc, batch)
@@ -168,6 +171,27 @@ def test_uneven_batch(cuda_device, prec, packed):
         ref = O.mci_direct(systems, gs[b], T[cls[b]], outputs=("f", "hilbert"))
         got = yh[out_off[b]:out_off[b] + out_len[b]].reshape(2, T[cls[b]])
         check(got, ref, prec)
+    plan.close()
+
+
+def test_host_classes_out_of_range(cuda_device):
+    plan = mci.Plan([F], [16, 32], [32, 64], max_batch=4)
+    x = torch.zeros(200, device="cuda")
+    y = torch.zeros(400, device="cuda")
+    with pytest.raises(mci.MciError) as ei:
+        mci.mci_interp_1d(plan.handle, x, None, y, None, np.array([0, 1, 7, 0], np.int32), 4)
+    assert ei.value.status == mci.MCI_ERR_INVALID_ARG
+    # repeated host-grouped calls reuse the two pinned staging blocks
+    cls = np.array([1, 0, 1, 0], np.int32)
+    g = torch.randn(16 + 32 + 16 + 32, device="cuda")
+    outs = []
+    for _ in range(5):
+        o = torch.empty(64 + 32 + 64 + 32, device="cuda")
+        mci.mci_interp_1d(plan.handle, g, None, o, None, cls, 4)
+        outs.append(o)
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
     plan.close()
 
 
