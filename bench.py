@@ -198,6 +198,70 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def images_2d_section(mci, torch, dev, timed, steps):
+    """Image workloads: SISR of 64 synthetic 512^2 images from x2 and x4 decimations, and an
+    uneven batch of 256 images (LR side in {128..1024}, scale in {2,3,4})."""
+    from paper_1802_10291_gb300 import synth
+    import oracle
+    sysd = [("identity",), ("deriv", 1)]
+    out = {}
+    # --- 64 x 512^2 HR, decimated by 2 and by 4
+    rng = synth.rng_for(2, 0)
+    hr_np = np.stack([synth.synthetic_image(rng, 512) for _ in range(64)]).astype(np.float32)
+    for s_ in (2, 4):
+        lr_np = synth.decimate(hr_np, s_)
+        L = lr_np.shape[-1]
+        plan = mci.Plan(sysd, L, s_ * L, channels="fd", max_batch=1, max_images=64,
+                        max_intermediate=64 * L * s_ * L)
+        lr = torch.tensor(lr_np.reshape(-1), device=dev)
+        hr = torch.empty(64 * 512 * 512, device=dev)
+        hh = np.full(64, L, np.int32)
+        ss = np.full(64, s_, np.int32)
+        n = max(20, steps)
+        t, _ = timed(lambda: plan.upsample_2d(lr, hh, hh, ss, hr, 64), n, 3)
+        ms = 1e3 * t / n
+        dh = torch.tensor(hh, device=dev)
+        ds = torch.tensor(ss, device=dev)
+        td, _ = timed(lambda: plan.upsample_2d(lr, dh, dh, ds, hr, 64), n, 3)
+        got = hr.view(64, 512, 512).cpu().numpy()
+        mse = np.mean((np.clip(got, 0, 1) - hr_np) ** 2, axis=(1, 2))
+        ref = oracle.upsample_2d(lr_np[0].astype(np.float64), s_, sysd)
+        err = float(np.max(np.abs(got[0] - ref)) / np.sqrt(np.mean(ref ** 2)))
+        bytes_ = 4 * (lr_np.size + hr_np.size)
+        out[f"sisr_64x512_s{s_}"] = {
+            "hr_mpixel_s": 64 * 512 * 512 / (ms / 1e3) / 1e6, "ms_per_batch": ms,
+            "device_grouped_ms": 1e3 * td / n,
+            "gbs_lr_plus_hr": bytes_ / (ms / 1e3) / 1e9,
+            "psnr_db_mean": float(np.mean(10 * np.log10(1.0 / mse))),
+            "err_vs_oracle_image0": err}
+        plan.close()
+    # --- 256 images, LR side ~ U{128..1024}, s ~ U{2,3,4}
+    rng = synth.rng_for(3, 0)
+    sides = [128, 256, 384, 512, 768, 1024]
+    scales = [2, 3, 4]
+    side = rng.choice(sides, 256)
+    sc = rng.choice(scales, 256)
+    pool = {L: [synth.synthetic_image(rng, L).astype(np.float32) for _ in range(4)] for L in sides}
+    imgs = [pool[int(L)][i % 4] for i, L in enumerate(side)]
+    PT = sorted({(int(L), int(L) * int(k)) for L in sides for k in scales})
+    inter = int(sum(int(L) * int(k) * int(L) for L, k in zip(side, sc)))
+    plan = mci.Plan(sysd, [p for p, _ in PT], [t for _, t in PT], channels="fd", max_batch=1,
+                    max_images=256, max_intermediate=inter)
+    lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), device=dev)
+    n_hr = int(sum(int(k) * int(k) * int(L) * int(L) for L, k in zip(side, sc)))
+    hr = torch.empty(n_hr, device=dev)
+    hh = np.ascontiguousarray(side, np.int32)
+    ss = np.ascontiguousarray(sc, np.int32)
+    n = max(5, steps // 10)
+    t, _ = timed(lambda: plan.upsample_2d(lr, hh, hh, ss, hr, 256), n, 3)
+    ms = 1e3 * t / n
+    out["uneven_256_images"] = {"hr_mpixel_s": n_hr / (ms / 1e3) / 1e6, "ms_per_batch": ms,
+                                "hr_pixels": n_hr, "gbs_lr_plus_hr": 4 * (lr.numel() + n_hr) / (ms / 1e3) / 1e9,
+                                "note": "LR images generated at LR size from a pool of 4 per side"}
+    plan.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,6 +367,9 @@ def main():
     k_ms = 1e3 * s4 / max(20, args.steps // 4)
     k_achieved = k_bytes / (k_ms / 1e3) / 1e9
 
+    # ---- image workloads (2-D)
+    images = images_2d_section(mci, torch, dev, timed, args.steps) if rank == 0 else None
+
     # ---- FP64 on the same batch
     plan64, x64, y64, _ = setup("fp64")
     steps64 = max(3, args.steps // 20)
@@ -376,6 +443,7 @@ def main():
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * secs64 / steps64,
                      "speedup_fp32_over_fp64": value / value64},
             "err_vs_oracle": err,
+            "images_2d": images,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * batch["n_in"] + plan32_stage_bytes,
                     "d2h_bytes_per_step": 4 * batch["n_out"]},

@@ -190,8 +190,14 @@ mci_status mci_interp_1d(mci_plan_t plan, const void* in, const int64_t* in_off,
  * image (the same class serves both when h == w).
  *   lr       device float, image i at lr + lr_off[i], h_i x w_i row-major
  *   lr_off   device int64 element offsets, or NULL (packed)
- *   h, w     device int arrays of image heights and widths
- *   scale    device int array of scale factors s_i >= 1
+ *   h, w     int arrays of image heights and widths
+ *   scale    int array of scale factors s_i >= 1.  h, w and scale all in DEVICE
+ *            memory: the batch is grouped on the device and launched from there
+ *            (stream-capturable; bad sizes set device_status bits).  All in HOST
+ *            memory: grouping on the host, one upload from pinned staging,
+ *            exact-grid launches per class from the host -- the faster path;
+ *            an image size the plan does not hold returns
+ *            MCI_ERR_UNSUPPORTED_SIZE; not for stream capture.
  *   hr       device float, image i at hr + hr_off[i], (s h) x (s w) row-major
  *   hr_off   device int64 element offsets, or NULL (packed)
  *   n_img    number of images, 0 .. max_images

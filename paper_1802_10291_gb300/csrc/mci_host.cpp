@@ -220,6 +220,13 @@ struct mci_plan_s {
     size_t stage_bytes = 0;
     size_t off_in_pref = 0, off_out_pref = 0, off_sched1 = 0;  // offsets inside the block
     int stage_cur = 0;
+    // host-grouped 2-D: staging mirrors the device block d_inter_off .. end of d_hws
+    int* d_hws = nullptr;                    // device copies of h, w, scale (3 x max_images)
+    char* h_stage2[2] = {nullptr, nullptr};
+    cudaEvent_t ev_stage2[2] = {nullptr, nullptr};
+    size_t stage2_bytes = 0;
+    size_t o2_lrp = 0, o2_hrp = 0, o2_it = 0, o2_s2 = 0, o2_hws = 0;
+    int stage2_cur = 0;
 };
 
 namespace {
@@ -411,6 +418,119 @@ static mci_status interp_1d_host_grouped(mci_plan_t p, KArgs a, const int* size_
     return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
 }
 
+// Launch every non-empty class of one pass from the host, each on its own stream,
+// forked from and joined back into s.
+static cudaError_t launch_classes(mci_plan_t p, const KArgs& tmpl, bool cols, const int* counts,
+                                  cudaStream_t s)
+{
+    cudaError_t e = cudaEventRecord(p->ev_fork, s);
+    for (int oi = 0; oi < (int)p->cls.size() && e == cudaSuccess; ++oi) {
+        const int c = p->order[oi];
+        if (counts[c] == 0) continue;
+        KArgs ac = tmpl;
+        ac.c = p->cdev[c];
+        ac.cls = c;
+        ac.W = p->launch[c].W;
+        void* args[] = {&ac};
+        const void* k = cols ? p->kern_cols[c] : p->kern[c];
+        e = cudaStreamWaitEvent(p->cstreams[c], p->ev_fork, 0);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(k, dim3((unsigned)counts[c]), dim3(kThreads), args,
+                                 (size_t)p->csmem[c], p->cstreams[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_join[c], p->cstreams[c]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[c], 0);
+    }
+    return e;
+}
+
+// 2-D batch whose image sizes are in host memory: per-class (image, tile) lists,
+// offsets and a device copy of the sizes are built on the host in pinned staging
+// (two alternating blocks), uploaded in one copy, then the row pass and the
+// column pass are launched per class from the host with exact grids.
+static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols, const int* h,
+                                           const int* w, const int* scale, bool pack_lr,
+                                           bool pack_hr, int64_t n_img, cudaStream_t s)
+{
+    const int n = (int)p->cls.size();
+    char* blk = p->h_stage2[p->stage2_cur];
+    cudaEvent_t ev = p->ev_stage2[p->stage2_cur];
+    if (cudaEventSynchronize(ev) != cudaSuccess) return MCI_ERR_CUDA;
+    int64_t* inter_off = (int64_t*)blk;
+    int64_t* lr_pref = (int64_t*)(blk + p->o2_lrp);
+    int64_t* hr_pref = (int64_t*)(blk + p->o2_hrp);
+    int2* items = (int2*)(blk + p->o2_it);
+    Sched2D* st = (Sched2D*)(blk + p->o2_s2);
+    int* hws = (int*)(blk + p->o2_hws);
+    const int64_t I = p->desc.max_images;
+    auto lookup = [&](int P, int64_t T) {
+        for (int c = 0; c < n; ++c)
+            if (p->cdev[c].P == P && p->cdev[c].T == T) return c;
+        return -1;
+    };
+    std::vector<int> rc(n_img), cc(n_img), rcnt(n, 0), ccnt(n, 0);
+    int64_t inter = 0, lr = 0, hrp = 0;
+    for (int64_t i = 0; i < n_img; ++i) {
+        const int hi = h[i], wi = w[i], si = scale[i];
+        if (hi <= 0 || wi <= 0 || si <= 0) return MCI_ERR_INVALID_ARG;
+        rc[i] = lookup(wi, (int64_t)si * wi);
+        cc[i] = lookup(hi, (int64_t)si * hi);
+        if (rc[i] < 0 || cc[i] < 0) return MCI_ERR_UNSUPPORTED_SIZE;
+        rcnt[rc[i]] += (hi + p->cdev[rc[i]].G - 1) / p->cdev[rc[i]].G;
+        ccnt[cc[i]] += (int)(((int64_t)si * wi + p->cdev[cc[i]].G - 1) / p->cdev[cc[i]].G);
+        inter_off[i] = inter;
+        lr_pref[i] = lr;
+        hr_pref[i] = hrp;
+        inter += (int64_t)hi * si * wi;
+        lr += (int64_t)hi * wi;
+        hrp += (int64_t)si * si * hi * wi;
+        hws[i] = hi;
+        hws[I + i] = wi;
+        hws[2 * I + i] = si;
+    }
+    if (inter > p->desc.max_intermediate) return MCI_ERR_UNSUPPORTED_SIZE;
+    int64_t pos = 0;
+    std::vector<int64_t> rcur(n), ccur(n);
+    for (int c = 0; c < n; ++c) {
+        st->row_start[c] = (int)pos;
+        st->row_count[c] = rcnt[c];
+        rcur[c] = pos;
+        pos += rcnt[c];
+    }
+    for (int c = 0; c < n; ++c) {
+        st->col_start[c] = (int)pos;
+        st->col_count[c] = ccnt[c];
+        ccur[c] = pos;
+        pos += ccnt[c];
+    }
+    if (pos > p->max_items) return MCI_ERR_UNSUPPORTED_SIZE;
+    for (int64_t i = 0; i < n_img; ++i) {
+        const int nr = (h[i] + p->cdev[rc[i]].G - 1) / p->cdev[rc[i]].G;
+        const int nc = (int)(((int64_t)scale[i] * w[i] + p->cdev[cc[i]].G - 1) / p->cdev[cc[i]].G);
+        for (int t = 0; t < nr; ++t) items[rcur[rc[i]]++] = make_int2((int)i, t);
+        for (int t = 0; t < nc; ++t) items[ccur[cc[i]]++] = make_int2((int)i, t);
+    }
+    // upload the used part: offsets and the filled items, then the schedule and sizes
+    const size_t head = p->o2_it + sizeof(int2) * (size_t)pos;
+    cudaError_t e = cudaMemcpyAsync(p->d_inter_off, blk, head, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char*)p->d_inter_off + p->o2_s2, blk + p->o2_s2, p->stage2_bytes - p->o2_s2,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, s);
+    p->stage2_cur ^= 1;
+    for (KArgs* a : {&rows, &cols}) {
+        a->h = p->d_hws;
+        a->w = p->d_hws + I;
+        a->scale = p->d_hws + 2 * I;
+        if (pack_lr) a->img_in_off = p->d_lr_pref;
+        if (pack_hr) a->img_out_off = p->d_hr_pref;
+    }
+    rows.mode = kModeRows;
+    cols.mode = kModeCols;
+    if (e == cudaSuccess) e = launch_classes(p, rows, false, rcnt.data(), s);
+    if (e == cudaSuccess) e = launch_classes(p, cols, true, ccnt.data(), s);
+    return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
 extern "C" {
 
 const char* mci_error_string(mci_status s)
@@ -440,6 +560,8 @@ mci_status mci_destroy(mci_plan_t p)
     for (int i = 0; i < 2; ++i) {
         if (p->ev_stage[i]) cudaEventDestroy(p->ev_stage[i]);
         if (p->h_stage[i]) cudaFreeHost(p->h_stage[i]);
+        if (p->ev_stage2[i]) cudaEventDestroy(p->ev_stage2[i]);
+        if (p->h_stage2[i]) cudaFreeHost(p->h_stage2[i]);
     }
     if (p->d_tables) cudaFree(p->d_tables);
     if (p->d_work) cudaFree(p->d_work);
@@ -474,7 +596,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         delete p;
         return MCI_ERR_CUDA;
     }
-    const int smem_cap = (int)prop.sharedMemPerBlockOptin - 1024;
+    const int smem_cap = (int)prop.sharedMemPerBlockOptin - 2048;  // static shared memory margin
     const int csz = (int)(2 * p->elem);
     int need = 0;
     int Pmax = 0, Tmax = 0;
@@ -559,12 +681,16 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         p->kern[c] = kernel_lookup(d.precision, false, p->cdev[c].N);
         p->kern_cols[c] = d.precision == MCI_FP32 ? kernel_lookup(d.precision, true, p->cdev[c].N) : nullptr;
         if (!p->kern[c]) e = cudaErrorInvalidDeviceFunction;
-        // Dynamic shared memory limit, and the largest shared-memory carveout: launches from
-        // the device-side scheduler do not get the carveout sized to their request, and
-        // without it fewer CTAs fit on an SM.
+        // The dynamic shared-memory limit is an attribute of the kernel function, which
+        // size classes of one FFT length (in this plan or another) share: it is set to
+        // the device maximum once; each launch states what it uses.  Largest carveout.
         for (const void* k : {p->kern[c], p->kern_cols[c]}) {
             if (!k || e != cudaSuccess) continue;
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
+            cudaFuncAttributes fa{};
+            e = cudaFuncGetAttributes(&fa, k);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
@@ -588,7 +714,8 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     const size_t o_inp = carve(sizeof(int64_t) * B);
     const size_t o_outp = carve(sizeof(int64_t) * B);
     const size_t o_s1 = carve(sizeof(Sched1D));
-    size_t o_inter = 0, o_ioff = 0, o_lrp = 0, o_hrp = 0, o_rc = 0, o_cc = 0, o_it = 0, o_s2 = 0;
+    size_t o_inter = 0, o_ioff = 0, o_lrp = 0, o_hrp = 0, o_rc = 0, o_cc = 0, o_it = 0, o_s2 = 0,
+           o_hws = 0;
     if (I > 0) {
         o_inter = carve(sizeof(float) * (size_t)X);
         o_ioff = carve(sizeof(int64_t) * I);
@@ -598,6 +725,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         o_cc = carve(sizeof(int) * I);
         o_it = carve(sizeof(int2) * (size_t)p->max_items);
         o_s2 = carve(sizeof(Sched2D));
+        o_hws = carve(sizeof(int) * 3 * I);
     }
     if (e == cudaSuccess) e = cudaMalloc(&p->d_work, off);
     if (e != cudaSuccess) {
@@ -621,6 +749,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         p->d_col_cls = (int*)(w + o_cc);
         p->d_items = (int2*)(w + o_it);
         p->d_sched2 = (Sched2D*)(w + o_s2);
+        p->d_hws = (int*)(w + o_hws);
     }
     // host-grouped path: one stream per class, fork/join events, two pinned staging blocks
     p->stage_bytes = o_s1 + sizeof(Sched1D) - o_sorted;
@@ -638,6 +767,27 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
             e = cudaHostAlloc((void**)&p->h_stage[i], p->stage_bytes, cudaHostAllocDefault);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_stage[i], cudaEventDisableTiming);
+        }
+    }
+    if (I > 0 && e == cudaSuccess) {
+        p->stage2_bytes = o_hws + sizeof(int) * 3 * I - o_ioff;
+        p->o2_lrp = o_lrp - o_ioff;
+        p->o2_hrp = o_hrp - o_ioff;
+        p->o2_it = o_it - o_ioff;
+        p->o2_s2 = o_s2 - o_ioff;
+        p->o2_hws = o_hws - o_ioff;
+        if (p->cstreams.empty()) {
+            p->cstreams.assign(n, nullptr);
+            p->ev_join.assign(n, nullptr);
+            for (int c = 0; c < n && e == cudaSuccess; ++c) {
+                e = cudaStreamCreateWithFlags(&p->cstreams[c], cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[c], cudaEventDisableTiming);
+            }
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        }
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaHostAlloc((void**)&p->h_stage2[i], p->stage2_bytes, cudaHostAllocDefault);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_stage2[i], cudaEventDisableTiming);
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int) * 4, s);
@@ -724,6 +874,13 @@ mci_status mci_upsample_2d(mci_plan_t p, const float* lr, const int64_t* lr_off,
     KArgs cols = rows;
     cols.in = p->d_inter;
     cols.out = hr;
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, h) != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return upsample_2d_host_grouped(p, rows, cols, h, w, scale, !lr_off, !hr_off, n_img, s);
     const int e = launch_sched_2d(n_img, (int)p->cls.size(), p->d_launch, p->desc.max_intermediate,
                                   p->max_items, p->d_inter_off, lr_off ? nullptr : p->d_lr_pref,
                                   hr_off ? nullptr : p->d_hr_pref, p->d_row_cls, p->d_col_cls,

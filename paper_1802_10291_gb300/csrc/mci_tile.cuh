@@ -171,7 +171,8 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 // Contiguous signals: signal g's M_in x P samples start at in + off[g].  Aligned
 // signals are copied with asynchronous 16-byte copies (all in flight at once);
-// the caller's barrier follows.
+// the caller's barrier follows.  Threads run over (signal, vector) pairs of the
+// whole tile, so short signals keep every thread busy.
 template <typename R>
 __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const R* __restrict__ in,
                                             const int64_t* off, int gcount)
@@ -179,71 +180,72 @@ __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const
     const int P = c.P, Min = c.M_in, npad = c.npad, QM = c.QM;
     const int per = Min * P;
     constexpr int VW = sizeof(R) == 4 ? 4 : 2;  // reals per 16-byte copy
-    bool async = false;
-    for (int g = 0; g < gcount; ++g) {
-        const R* src = in + off[g];
-        cpx<R>* dst = sm + g * QM * npad;
-        const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (P % VW == 0);
-        if (vec) {
-            async = true;
-            for (int t = ltid(); t < per / VW; t += blockDim.x) {
-                const int i = t * VW;
-                const int m = i / P, p = (i - m * P) >> 1;
-                cp_async16(&dst[m * npad + pad16(p)], src + i);
-            }
-        } else {
-            for (int i = ltid(); i < per; i += blockDim.x) {
-                const int m = i / P, pp = i - m * P;
-                R* d = reinterpret_cast<R*>(&dst[m * npad + pad16(pp >> 1)]);
-                d[pp & 1] = src[i];
-            }
+    bool vec = (P % VW) == 0;
+    for (int g = 0; g < gcount; ++g) vec = vec && ((reinterpret_cast<uintptr_t>(in + off[g]) & 15) == 0);
+    if (vec) {
+        const int nv = per / VW;
+        for (int t = ltid(); t < gcount * nv; t += blockDim.x) {
+            const int g = t / nv, v = t - g * nv;
+            const int i = v * VW;
+            const int m = i / P, p = (i - m * P) >> 1;
+            cp_async16(&sm[(g * QM + m) * npad + pad16(p)], in + off[g] + i);
+        }
+        cp_async_wait_all();
+    } else {
+        for (int t = ltid(); t < gcount * per; t += blockDim.x) {
+            const int g = t / per, i = t - g * per;
+            const int m = i / P, pp = i - m * P;
+            R* d = reinterpret_cast<R*>(&sm[(g * QM + m) * npad + pad16(pp >> 1)]);
+            d[pp & 1] = in[off[g] + i];
         }
     }
-    if (async) cp_async_wait_all();
 }
 
 // Contiguous outputs: output o of signal g at out + off[g] + o * T, T = s P samples;
-// sample j = s * (2l + e) + u is component e of phase (o, u) at position l.
+// sample j = s * (2l + e) + u is component e of phase (o, u) at position l.  Threads
+// run over (signal, vector) pairs of the whole tile.
 template <typename R>
 __device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
                                              const int64_t* off, int gcount)
 {
     const int T = c.T, s = c.s, npad = c.npad, QM = c.QM, nout = c.n_out;
     const int per = nout * T;
-    for (int g = 0; g < gcount; ++g) {
-        R* dst = out + off[g];
-        const cpx<R>* srcs = sm + g * QM * npad;
-        const bool vec = ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && (T % 4 == 0);
-        if (vec) {
-            for (int t = ltid(); t < per / 4; t += blockDim.x) {
-                const int i0 = t * 4;
-                const int o = i0 / T;
-                const int x0 = i0 - o * T;
-                int l2 = x0 / s, u = x0 - l2 * s;   // sample x = s * l2 + u
-                R v[4];
+    bool vec = (T % 4) == 0;
+    for (int g = 0; g < gcount; ++g) vec = vec && ((reinterpret_cast<uintptr_t>(out + off[g]) & 15) == 0);
+    if (vec) {
+        const int nv = per / 4;
+        for (int t = ltid(); t < gcount * nv; t += blockDim.x) {
+            const int g = t / nv, v = t - g * nv;
+            const cpx<R>* srcs = sm + g * QM * npad;
+            R* dst = out + off[g];
+            const int i0 = v * 4;
+            const int o = i0 / T;
+            const int x0 = i0 - o * T;
+            int l2 = x0 / s, u = x0 - l2 * s;   // sample x = s * l2 + u
+            R val[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const cpx<R> z = srcs[(o * s + u) * npad + pad16(l2 >> 1)];
-                    v[e] = (l2 & 1) ? z.y : z.x;
-                    if (++u == s) {
-                        u = 0;
-                        ++l2;
-                    }
-                }
-                if constexpr (sizeof(R) == 4) {
-                    reinterpret_cast<float4*>(dst)[t] = make_float4(v[0], v[1], v[2], v[3]);
-                } else {
-                    reinterpret_cast<double2*>(dst)[2 * t] = make_double2(v[0], v[1]);
-                    reinterpret_cast<double2*>(dst)[2 * t + 1] = make_double2(v[2], v[3]);
-                }
-            }
-        } else {
-            for (int i = ltid(); i < per; i += blockDim.x) {
-                const int o = i / T, x = i - o * T;
-                const int l2 = x / s, u = x - l2 * s;
+            for (int e = 0; e < 4; ++e) {
                 const cpx<R> z = srcs[(o * s + u) * npad + pad16(l2 >> 1)];
-                dst[i] = (l2 & 1) ? z.y : z.x;
+                val[e] = (l2 & 1) ? z.y : z.x;
+                if (++u == s) {
+                    u = 0;
+                    ++l2;
+                }
             }
+            if constexpr (sizeof(R) == 4) {
+                reinterpret_cast<float4*>(dst)[v] = make_float4(val[0], val[1], val[2], val[3]);
+            } else {
+                reinterpret_cast<double2*>(dst)[2 * v] = make_double2(val[0], val[1]);
+                reinterpret_cast<double2*>(dst)[2 * v + 1] = make_double2(val[2], val[3]);
+            }
+        }
+    } else {
+        for (int t = ltid(); t < gcount * per; t += blockDim.x) {
+            const int g = t / per, i = t - g * per;
+            const int o = i / T, x = i - o * T;
+            const int l2 = x / s, u = x - l2 * s;
+            const cpx<R> z = sm[(g * QM + o * s + u) * npad + pad16(l2 >> 1)];
+            out[off[g] + i] = (l2 & 1) ? z.y : z.x;
         }
     }
 }

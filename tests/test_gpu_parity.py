@@ -215,10 +215,12 @@ def test_empty_batch_is_noop(cuda_device):
     plan.close()
 
 
-def test_upsample_2d_matches_oracle(cuda_device):
-    """Rows then columns (Section 5.2), FD derivative channel, images of different sizes."""
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_upsample_2d_matches_oracle(cuda_device, where):
+    """Rows then columns (Section 5.2), FD derivative channel, images of different sizes;
+    image sizes in device memory (device-side grouping) or host memory (host-side)."""
     systems = [F, D1]
-    shapes = [(16, 16, 2), (32, 16, 4), (12, 24, 3), (16, 32, 2)]
+    shapes = [(16, 16, 2), (32, 16, 4), (12, 24, 3), (16, 32, 2), (16, 16, 3), (32, 32, 2)]
     sizes = sorted({(w, s * w) for h, w, s in shapes} | {(h, s * h) for h, w, s in shapes})
     plan = mci.Plan(systems, [p for p, _ in sizes], [t for _, t in sizes], channels="fd",
                     max_batch=1, max_images=len(shapes),
@@ -228,9 +230,10 @@ def test_upsample_2d_matches_oracle(cuda_device):
     lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), dtype=torch.float32, device="cuda")
     hr_len = [s * s * h * w for h, w, s in shapes]
     hr = torch.full((sum(hr_len),), float("nan"), device="cuda")
-    hh = torch.tensor([h for h, w, s in shapes], dtype=torch.int32, device="cuda")
-    ww = torch.tensor([w for h, w, s in shapes], dtype=torch.int32, device="cuda")
-    ss = torch.tensor([s for h, w, s in shapes], dtype=torch.int32, device="cuda")
+    dev = "cuda" if where == "device" else "cpu"
+    hh = torch.tensor([h for h, w, s in shapes], dtype=torch.int32, device=dev)
+    ww = torch.tensor([w for h, w, s in shapes], dtype=torch.int32, device=dev)
+    ss = torch.tensor([s for h, w, s in shapes], dtype=torch.int32, device=dev)
     plan.upsample_2d(lr, hh, ww, ss, hr, len(shapes))
     torch.cuda.synchronize()
     assert plan.info()["device_status"] == 0
