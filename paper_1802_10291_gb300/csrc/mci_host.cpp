@@ -227,6 +227,14 @@ struct mci_plan_s {
     size_t stage2_bytes = 0;
     size_t o2_lrp = 0, o2_hrp = 0, o2_it = 0, o2_s2 = 0, o2_hws = 0;
     int stage2_cur = 0;
+    // tensor-core image path: per class offset of the T x P matrix in gemm_tab (-1: none)
+    std::vector<float> gemm_tab;
+    std::vector<int64_t> gemm_off;
+    std::vector<const float*> d_kmap;
+    void* d_gemm = nullptr;
+    GemmJob* d_jobs = nullptr;
+    int* d_tile0 = nullptr;
+    size_t o2_jobs = 0, o2_tile0 = 0;
 };
 
 namespace {
@@ -293,6 +301,16 @@ void push_cpx(std::vector<R>& v, cd z)
     v.push_back((R)z.imag());
 }
 
+// Image size classes small enough for the tensor-core path: the T x P matrix of the
+// linear map is formed by the plan, and both passes of an image run as GEMMs when
+// its row and column classes are both eligible.
+bool gemm_eligible(const mci_plan_s* p, const HostClass& hc)
+{
+    const mci_desc& d = p->desc;
+    return d.max_images > 0 && d.precision == MCI_FP32 && p->M_in == 1 && p->n_out == 1 &&
+           hc.P % 128 == 0 && hc.P <= 256 && hc.T % 128 == 0 && hc.T <= 2048;
+}
+
 template <typename R>
 mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
 {
@@ -331,6 +349,9 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
         };
         auto res = [&](int k) { return (int)((((int64_t)k - hc.N1) % P + P) % P); };
         std::vector<cd> Wk((size_t)M * Q);
+        const bool gemm = gemm_eligible(p, hc);
+        std::vector<cd> w1;  // single-input-channel weights per bin, phase (GEMM matrix)
+        if (gemm) w1.assign((size_t)(N + 1) * Q, 0.0);
         for (int k = 0; k <= N; ++k) {
             const int ra = res(k), rb = res((P - k) % P);
             for (int m = 0; m < M; ++m)
@@ -341,10 +362,30 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
                     cd acc = 0.0;
                     for (int m = 0; m < M; ++m) acc += fd_factor(d.sys[m], P, k) * Wk[(size_t)m * Q + q];
                     push_cpx(W, acc);
+                    if (gemm) w1[(size_t)k * Q + q] = acc;
                 }
             } else {
                 for (int m = 0; m < Min; ++m)
                     for (int q = 0; q < Q; ++q) push_cpx(W, Wk[(size_t)m * Q + q]);
+                if (gemm)
+                    for (int q = 0; q < Q; ++q) w1[(size_t)k * Q + q] = Wk[q];
+            }
+        }
+        if (gemm) {
+            // out[s l + u] = sum_p kappa_u[(l - p) mod P] x[p], kappa_u[d] = sum over all P bins of
+            // W_k[u] e^{2 pi i k d / P} with W_{P-k} = conj W_k (the kernel's real inverse FFT)
+            p->gemm_off[c] = (int64_t)p->gemm_tab.size();
+            std::vector<double> kappa((size_t)s * P);
+            for (int u = 0; u < s; ++u)
+                for (int dd = 0; dd < P; ++dd) {
+                    double acc = w1[(size_t)0 * Q + u].real() + w1[(size_t)N * Q + u].real() * ((dd & 1) ? -1.0 : 1.0);
+                    for (int k = 1; k < N; ++k) acc += 2.0 * (w1[(size_t)k * Q + u] * cis_frac((int64_t)k * dd, P)).real();
+                    kappa[(size_t)u * P + dd] = acc;
+                }
+            for (int j = 0; j < T; ++j) {
+                const int l = j / s, u = j % s;
+                for (int q = 0; q < P; ++q)
+                    p->gemm_tab.push_back((float)kappa[(size_t)u * P + (((l - q) % P) + P) % P]);
             }
         }
     }
@@ -468,6 +509,10 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
         return -1;
     };
     std::vector<int> rc(n_img), cc(n_img), rcnt(n, 0), ccnt(n, 0);
+    std::vector<char> by_gemm(n_img, 0);
+    GemmJob* jobs = (GemmJob*)(blk + p->o2_jobs);     // row jobs, then column jobs at + I
+    int* tile0 = (int*)(blk + p->o2_tile0);            // row prefix, then column prefix at + I + 1
+    int n_gemm = 0, row_tiles = 0, col_tiles = 0;
     int64_t inter = 0, lr = 0, hrp = 0;
     for (int64_t i = 0; i < n_img; ++i) {
         const int hi = h[i], wi = w[i], si = scale[i];
@@ -475,8 +520,46 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
         rc[i] = lookup(wi, (int64_t)si * wi);
         cc[i] = lookup(hi, (int64_t)si * hi);
         if (rc[i] < 0 || cc[i] < 0) return MCI_ERR_UNSUPPORTED_SIZE;
-        rcnt[rc[i]] += (hi + p->cdev[rc[i]].G - 1) / p->cdev[rc[i]].G;
-        ccnt[cc[i]] += (int)(((int64_t)si * wi + p->cdev[cc[i]].G - 1) / p->cdev[cc[i]].G);
+        if (p->d_kmap[rc[i]] && p->d_kmap[cc[i]]) {
+            // both passes on the tensor cores: Y^T = (X K_w^T)^T into the intermediate, HR = K_h Y
+            by_gemm[i] = 1;
+            GemmJob& r = jobs[n_gemm];
+            r.A = (const float*)rows.in + (pack_lr ? lr : 0);
+            r.a_off = pack_lr ? nullptr : rows.img_in_off;
+            r.B = p->d_kmap[rc[i]];
+            r.C = p->d_inter + inter;
+            r.c_off = nullptr;
+            r.lda = wi;
+            r.ldb = wi;
+            r.ldc = hi;
+            r.M = hi;
+            r.N = si * wi;
+            r.K = wi;
+            r.img = (int)i;
+            r.transpose_c = 1;
+            GemmJob& q = jobs[I + n_gemm];
+            q.A = p->d_kmap[cc[i]];
+            q.a_off = nullptr;
+            q.B = p->d_inter + inter;
+            q.C = (float*)cols.out + (pack_hr ? hrp : 0);
+            q.c_off = pack_hr ? nullptr : cols.img_out_off;
+            q.lda = hi;
+            q.ldb = hi;
+            q.ldc = (int64_t)si * wi;
+            q.M = si * hi;
+            q.N = si * wi;
+            q.K = hi;
+            q.img = (int)i;
+            q.transpose_c = 0;
+            tile0[n_gemm] = row_tiles;
+            tile0[I + 1 + n_gemm] = col_tiles;
+            row_tiles += (r.M / 128) * (r.N / 128);
+            col_tiles += (q.M / 128) * (q.N / 128);
+            ++n_gemm;
+        } else {
+            rcnt[rc[i]] += (hi + p->cdev[rc[i]].G - 1) / p->cdev[rc[i]].G;
+            ccnt[cc[i]] += (int)(((int64_t)si * wi + p->cdev[cc[i]].G - 1) / p->cdev[cc[i]].G);
+        }
         inter_off[i] = inter;
         lr_pref[i] = lr;
         hr_pref[i] = hrp;
@@ -503,7 +586,10 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
         pos += ccnt[c];
     }
     if (pos > p->max_items) return MCI_ERR_UNSUPPORTED_SIZE;
+    tile0[n_gemm] = row_tiles;
+    tile0[I + 1 + n_gemm] = col_tiles;
     for (int64_t i = 0; i < n_img; ++i) {
+        if (by_gemm[i]) continue;
         const int nr = (h[i] + p->cdev[rc[i]].G - 1) / p->cdev[rc[i]].G;
         const int nc = (int)(((int64_t)scale[i] * w[i] + p->cdev[cc[i]].G - 1) / p->cdev[cc[i]].G);
         for (int t = 0; t < nr; ++t) items[rcur[rc[i]]++] = make_int2((int)i, t);
@@ -526,7 +612,11 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
     }
     rows.mode = kModeRows;
     cols.mode = kModeCols;
+    if (e == cudaSuccess && n_gemm)
+        e = (cudaError_t)launch_gemm(p->d_jobs, p->d_tile0, n_gemm, row_tiles, p->d_status, s);
     if (e == cudaSuccess) e = launch_classes(p, rows, false, rcnt.data(), s);
+    if (e == cudaSuccess && n_gemm)
+        e = (cudaError_t)launch_gemm(p->d_jobs + I, p->d_tile0 + I + 1, n_gemm, col_tiles, p->d_status, s);
     if (e == cudaSuccess) e = launch_classes(p, cols, true, ccnt.data(), s);
     return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
 }
@@ -565,6 +655,7 @@ mci_status mci_destroy(mci_plan_t p)
     }
     if (p->d_tables) cudaFree(p->d_tables);
     if (p->d_work) cudaFree(p->d_work);
+    if (p->d_gemm) cudaFree(p->d_gemm);
     delete p;
     return MCI_OK;
 }
@@ -646,6 +737,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
                      [&](int a, int b) { return p->cls[a].P > p->cls[b].P; });
 
     // FP64 tables
+    p->gemm_off.assign(n, -1);
     std::vector<float> W32;
     std::vector<double> W64;
     st = d.precision == MCI_FP64 ? build_tables<double>(p, W64) : build_tables<float>(p, W32);
@@ -699,6 +791,17 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_launch, p->launch.data(), sizeof(ClassLaunch) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_order, p->order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_W, W_src, W_bytes, cudaMemcpyHostToDevice, s);
+    p->d_kmap.assign(n, nullptr);
+    if (e == cudaSuccess && !p->gemm_tab.empty()) {
+        e = cudaMalloc(&p->d_gemm, sizeof(float) * p->gemm_tab.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_gemm, p->gemm_tab.data(), sizeof(float) * p->gemm_tab.size(),
+                                cudaMemcpyHostToDevice, s);
+        for (int c = 0; c < n; ++c)
+            if (p->gemm_off[c] >= 0) p->d_kmap[c] = (const float*)p->d_gemm + p->gemm_off[c];
+        if (e == cudaSuccess) e = (cudaError_t)prepare_gemm();
+        p->table_bytes += (int64_t)(sizeof(float) * p->gemm_tab.size());
+    }
 
     // workspace
     const int64_t B = d.max_batch, I = d.max_images, X = d.max_intermediate;
@@ -715,7 +818,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     const size_t o_outp = carve(sizeof(int64_t) * B);
     const size_t o_s1 = carve(sizeof(Sched1D));
     size_t o_inter = 0, o_ioff = 0, o_lrp = 0, o_hrp = 0, o_rc = 0, o_cc = 0, o_it = 0, o_s2 = 0,
-           o_hws = 0;
+           o_hws = 0, o_jobs = 0, o_tile0 = 0;
     if (I > 0) {
         o_inter = carve(sizeof(float) * (size_t)X);
         o_ioff = carve(sizeof(int64_t) * I);
@@ -726,6 +829,8 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         o_it = carve(sizeof(int2) * (size_t)p->max_items);
         o_s2 = carve(sizeof(Sched2D));
         o_hws = carve(sizeof(int) * 3 * I);
+        o_jobs = carve(sizeof(GemmJob) * 2 * I);
+        o_tile0 = carve(sizeof(int) * 2 * (I + 1));
     }
     if (e == cudaSuccess) e = cudaMalloc(&p->d_work, off);
     if (e != cudaSuccess) {
@@ -750,6 +855,8 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         p->d_items = (int2*)(w + o_it);
         p->d_sched2 = (Sched2D*)(w + o_s2);
         p->d_hws = (int*)(w + o_hws);
+        p->d_jobs = (GemmJob*)(w + o_jobs);
+        p->d_tile0 = (int*)(w + o_tile0);
     }
     // host-grouped path: one stream per class, fork/join events, two pinned staging blocks
     p->stage_bytes = o_s1 + sizeof(Sched1D) - o_sorted;
@@ -770,7 +877,9 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         }
     }
     if (I > 0 && e == cudaSuccess) {
-        p->stage2_bytes = o_hws + sizeof(int) * 3 * I - o_ioff;
+        p->stage2_bytes = o_tile0 + sizeof(int) * 2 * (I + 1) - o_ioff;
+        p->o2_jobs = o_jobs - o_ioff;
+        p->o2_tile0 = o_tile0 - o_ioff;
         p->o2_lrp = o_lrp - o_ioff;
         p->o2_hrp = o_hrp - o_ioff;
         p->o2_it = o_it - o_ioff;

@@ -91,6 +91,21 @@ enum StatusBits {
     kStatusBatch = 8,
     kStatusIntermediate = 16,
     kStatusLaunch = 32,
+    kStatusTimeout = 64,
+};
+
+// One GEMM of the small-P image path: C[M x N] = A[M x K] * B[N x K]^T (FP32 operands,
+// split into BF16 planes on the tensor cores), C stored row-major or transposed.
+struct GemmJob {
+    const float* A;          // plus a_off[img] when a_off is set
+    const float* B;
+    float* C;                // plus c_off[img] when c_off is set
+    const int64_t* a_off;    // device per-image offsets, or NULL
+    const int64_t* c_off;
+    int64_t lda, ldb, ldc;
+    int M, N, K;
+    int img;
+    int transpose_c;
 };
 
 // Device-built work lists of one mci_upsample_2d call: per size class, the
@@ -141,6 +156,12 @@ int launch_sched_2d(int64_t n_img, int n_classes, const ClassLaunch* cl, int64_t
                     int64_t max_items, int64_t* inter_off, int64_t* lr_pref, int64_t* hr_pref,
                     int* row_cls, int* col_cls, int2* items, Sched2D* st, const KArgs& rows_tmpl,
                     const KArgs& cols_tmpl, void* stream);
+
+// Tensor-core GEMM (mci_gemm.cu): tile0 is the tile prefix over jobs (n_jobs + 1).
+int launch_gemm(const GemmJob* jobs, const int* tile0, int n_jobs, int n_tiles, int* status,
+                void* stream);
+int prepare_gemm();
+int gemm_smem_bytes();
 
 // Static scratch of mci_interp_1d_noalloc (mci_noalloc.cu).
 struct NoAllocScratch;
