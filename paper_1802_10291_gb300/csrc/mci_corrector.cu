@@ -1,0 +1,514 @@
+// Learned residual corrector on top of MCI upsampling, and an on-device
+// generator of the synthetic training images.
+//
+// Network: pred = mci + f(mci), f = conv5 o relu o conv4 o relu o conv3 o relu o
+// conv2 o relu o conv1, every conv 3x3 with bias and periodic padding (images
+// are periodic in the interpolation model), channels 1 -> 32 -> 32 -> 32 -> 32 -> 1.
+// Weights are BF16 in the forward and backward passes (FP32 master copies in
+// the optimizer), activations and accumulation FP32.  Loss: mean squared error
+// of pred against the HR image.  Training: Adam.
+//
+// Kernels (CUDA cores, one 16 x 16 pixel tile of one image per CTA):
+//   conv_fwd      out[co] = b[co] + sum_ci sum_taps w[co][ci][t] x[ci](p + d_t), optional
+//                 ReLU, optional residual add;
+//   conv_bwd_data gin[ci] = sum_co sum_taps w[co][ci][t] g[co](p - d_t), g masked by the
+//                 layer's ReLU (the same kernel with the weights transposed and the
+//                 taps reversed);
+//   conv_bwd_w    gw[co][ci][t] = sum_p g[co](p) x[ci](p + d_t), gb[co] = sum_p g[co](p),
+//                 per-CTA partial sums reduced with atomics;
+//   mse, adam, image generator.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mci_corrector.h"
+
+namespace {
+
+constexpr int kTile = 16;          // output tile edge
+constexpr int kHalo = kTile + 2;   // input tile edge
+constexpr int kCThreads = kTile * kTile;
+constexpr int kWide = 32;          // hidden channels
+constexpr int kLayers = 5;
+__host__ __device__ constexpr int cin_of(int l) { return l == 0 ? 1 : kWide; }
+__host__ __device__ constexpr int cout_of(int l) { return l == kLayers - 1 ? 1 : kWide; }
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ---------------------------------------------------------------------------
+// forward conv (also the data-gradient conv): COUT output channels per pixel
+// ---------------------------------------------------------------------------
+// x: [B][cin][H][W]; w: bf16 [COUT][cin][9] (forward) -- when transposed_w, the weights
+// are read as w[ci][co][8 - t] from a [cin_fwd = COUT... ] tensor laid out [cin][COUT][9]
+// (i.e. the forward tensor of the layer whose data gradient this is).
+// mask: optional [B][cin][H][W] ReLU mask source (x *= (mask > 0)).
+template <int COUT>
+__global__ void __launch_bounds__(kCThreads) conv3x3_kernel(
+    const float* __restrict__ x, int cin, const __nv_bfloat16* __restrict__ w, bool transposed_w,
+    const float* __restrict__ bias, const float* __restrict__ mask, const float* __restrict__ res,
+    float* __restrict__ out, int H, int W, bool relu)
+{
+    extern __shared__ float csm[];
+    float* xs = csm;                          // [cin][18][18]
+    float* ws = csm + cin * kHalo * kHalo;    // [cin][9][COUT]
+    const int b = blockIdx.z;
+    const int y0 = blockIdx.y * kTile, x0 = blockIdx.x * kTile;
+    const int tid = threadIdx.x;
+    const int64_t plane = (int64_t)H * W;
+    for (int i = tid; i < cin * kHalo * kHalo; i += kCThreads) {
+        const int ci = i / (kHalo * kHalo), r = i % (kHalo * kHalo);
+        const int yy = wrap(y0 + r / kHalo - 1, H), xx = wrap(x0 + r % kHalo - 1, W);
+        const int64_t gi = ((int64_t)b * cin + ci) * plane + (int64_t)yy * W + xx;
+        float v = x[gi];
+        if (mask && !(mask[gi] > 0.f)) v = 0.f;
+        xs[i] = v;
+    }
+    for (int i = tid; i < cin * 9 * COUT; i += kCThreads) {
+        const int ci = i / (9 * COUT), t = (i / COUT) % 9, co = i % COUT;
+        const float wv = transposed_w ? __bfloat162float(w[((int64_t)ci * COUT + co) * 9 + (8 - t)])
+                                      : __bfloat162float(w[((int64_t)co * cin + ci) * 9 + t]);
+        ws[i] = wv;
+    }
+    __syncthreads();
+    const int ty = tid / kTile, tx = tid % kTile;
+    float acc[COUT];
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) acc[co] = bias ? bias[co] : 0.f;
+    for (int ci = 0; ci < cin; ++ci) {
+        const float* xc = xs + ci * kHalo * kHalo;
+        const float* wc = ws + ci * 9 * COUT;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const float v = xc[(ty + t / 3) * kHalo + tx + t % 3];
+            if constexpr (COUT % 4 == 0) {
+#pragma unroll
+                for (int co = 0; co < COUT; co += 4) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(wc + t * COUT + co);
+                    acc[co] += v * w4.x;
+                    acc[co + 1] += v * w4.y;
+                    acc[co + 2] += v * w4.z;
+                    acc[co + 3] += v * w4.w;
+                }
+            } else {
+#pragma unroll
+                for (int co = 0; co < COUT; ++co) acc[co] += v * wc[t * COUT + co];
+            }
+        }
+    }
+    const int y = y0 + ty, xq = x0 + tx;
+    if (y < H && xq < W) {
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) {
+            const int64_t o = ((int64_t)b * COUT + co) * plane + (int64_t)y * W + xq;
+            float v = acc[co];
+            if (relu) v = fmaxf(v, 0.f);
+            if (res) v += res[o];
+            out[o] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: gw[co][ci][t] += sum_p g[co](p) x[ci](p + d_t), gb[co] += sum_p g[co](p)
+// g masked by the layer's ReLU output (gmask) when given.  One CTA per (tile, image);
+// thread t owns (co = t % COUT, ci block of CIB) x 9 taps.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kCThreads) conv3x3_wgrad_kernel(
+    const float* __restrict__ x, const float* __restrict__ g, const float* __restrict__ gmask,
+    float* __restrict__ gw, float* __restrict__ gb, int H, int W)
+{
+    extern __shared__ float csm[];
+    float* xs = csm;                          // [CIN][18][18]
+    float* gs = csm + CIN * kHalo * kHalo;    // [COUT][16][16]
+    const int b = blockIdx.z;
+    const int y0 = blockIdx.y * kTile, x0 = blockIdx.x * kTile;
+    const int tid = threadIdx.x;
+    const int64_t plane = (int64_t)H * W;
+    for (int i = tid; i < CIN * kHalo * kHalo; i += kCThreads) {
+        const int ci = i / (kHalo * kHalo), r = i % (kHalo * kHalo);
+        const int yy = wrap(y0 + r / kHalo - 1, H), xx = wrap(x0 + r % kHalo - 1, W);
+        xs[i] = x[((int64_t)b * CIN + ci) * plane + (int64_t)yy * W + xx];
+    }
+    for (int i = tid; i < COUT * kTile * kTile; i += kCThreads) {
+        const int co = i / (kTile * kTile), r = i % (kTile * kTile);
+        const int yy = y0 + r / kTile, xx = x0 + r % kTile;
+        float v = 0.f;
+        if (yy < H && xx < W) {
+            const int64_t gi = ((int64_t)b * COUT + co) * plane + (int64_t)yy * W + xx;
+            v = g[gi];
+            if (gmask && !(gmask[gi] > 0.f)) v = 0.f;
+        }
+        gs[i] = v;
+    }
+    __syncthreads();
+    constexpr int PAIRS = CIN * COUT;                     // (co, ci) pairs
+    constexpr int PER = (PAIRS + kCThreads - 1) / kCThreads;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int pr = tid + k * kCThreads;
+        if (pr < PAIRS) {
+            const int co = pr % COUT, ci = pr / COUT;
+            float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            float accb = 0.f;
+            const float* xc = xs + ci * kHalo * kHalo;
+            const float* gc = gs + co * kTile * kTile;
+            for (int p = 0; p < kTile * kTile; ++p) {
+                const float gv = gc[p];
+                const int py = p / kTile, px = p % kTile;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc[t] += gv * xc[(py + t / 3) * kHalo + px + t % 3];
+                accb += gv;
+            }
+#pragma unroll
+            for (int t = 0; t < 9; ++t) atomicAdd(&gw[((int64_t)co * CIN + ci) * 9 + t], acc[t]);
+            if (ci == 0) atomicAdd(&gb[co], accb);
+        }
+    }
+}
+
+// d pred: grad = 2 (pred - hr) / n, loss += sum (pred - hr)^2 / n
+__global__ void mse_kernel(const float* __restrict__ pred, const float* __restrict__ hr, float* __restrict__ grad,
+                           float* __restrict__ loss, int64_t n)
+{
+    float part = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = pred[i] - hr[i];
+        if (grad) grad[i] = 2.f * d / (float)n;
+        part += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, part / (float)n);
+}
+
+// Adam on FP32 master weights; refresh the BF16 copy used by the convolutions.
+__global__ void adam_kernel(float* __restrict__ master, __nv_bfloat16* __restrict__ wbf,
+                            const float* __restrict__ grad, float* __restrict__ m1, float* __restrict__ m2,
+                            int n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grad[i];
+    const float a = b1 * m1[i] + (1.f - b1) * g;
+    const float v = b2 * m2[i] + (1.f - b2) * g * g;
+    m1[i] = a;
+    m2[i] = v;
+    const float wv = master[i] - lr * (a / c1) / (sqrtf(v / c2) + eps);
+    master[i] = wv;
+    if (wbf) wbf[i] = __float2bfloat16_rn(wv);
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// ---------------------------------------------------------------------------
+// synthetic images: 0.5 + 20 anisotropic Gaussian blobs + 10 straight edges
+// + 8 low-frequency waves of amplitude 0.01, clipped to [0, 1].  Parameters per image
+// (host-drawn, seeded): blobs (cy, cx, 1/s_major, 1/s_minor, angle, amp), edges
+// (py, px, angle, step), waves (fy, fx, phase, amp) -- all in pixel units.
+// ---------------------------------------------------------------------------
+__global__ void image_gen_kernel(const float* __restrict__ prm, float* __restrict__ img, int H, int W)
+{
+    const int b = blockIdx.z;
+    const float* q = prm + (int64_t)b * MCI_IMAGE_PARAMS;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= H || x >= W) return;
+    float v = 0.5f;
+    for (int k = 0; k < 20; ++k) {
+        const float* p = q + 6 * k;
+        const float dy = y - p[0], dx = x - p[1];
+        float sa, ca;
+        sincosf(p[4], &sa, &ca);
+        const float u = (dx * ca + dy * sa) * p[2], w = (-dx * sa + dy * ca) * p[3];
+        v += p[5] * __expf(-0.5f * (u * u + w * w));
+    }
+    for (int k = 0; k < 10; ++k) {
+        const float* p = q + 120 + 4 * k;
+        float sa, ca;
+        sincosf(p[2], &sa, &ca);
+        if ((x - p[1]) * sa - (y - p[0]) * ca > 0.f) v += p[3];
+    }
+    for (int k = 0; k < 8; ++k) {
+        const float* p = q + 160 + 4 * k;
+        float t = p[0] * y / H + p[1] * x / W;     // integer cycles: reduce to [-1/2, 1/2]
+        t -= rintf(t);
+        v += p[3] * __cosf(6.2831853f * t + p[2]);
+    }
+    img[((int64_t)b * H + y) * W + x] = fminf(fmaxf(v, 0.f), 1.f);
+}
+
+// pure decimation LR[y][x] = HR[s y][s x]
+__global__ void decimate_kernel(const float* __restrict__ hr, float* __restrict__ lr, int H, int W, int s)
+{
+    const int b = blockIdx.z;
+    const int h = H / s, w = W / s;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= h || x >= w) return;
+    lr[((int64_t)b * h + y) * w + x] = hr[((int64_t)b * H + (int64_t)s * y) * W + (int64_t)s * x];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct mci_corrector_s {
+    int64_t max_pixels = 0;
+    int n_params = 0;
+    int woff[kLayers], boff[kLayers];
+    float* master = nullptr;        // FP32 master weights and biases (flat)
+    __nv_bfloat16* wbf = nullptr;   // BF16 copy
+    float* grad = nullptr;
+    float* m1 = nullptr;
+    float* m2 = nullptr;
+    float* act = nullptr;           // layer outputs: kLayers - 1 hidden [B][32][H][W] + pred
+    float* gbuf[2] = {nullptr, nullptr};
+    float* loss = nullptr;
+    int step = 0;
+};
+
+namespace {
+
+int corrector_param_layout(int* woff, int* boff)
+{
+    int n = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        woff[l] = n;
+        n += cout_of(l) * cin_of(l) * 9;
+        boff[l] = n;
+        n += cout_of(l);
+    }
+    return n;
+}
+
+cudaError_t conv(const float* x, int cin, int cout, const __nv_bfloat16* w, bool tw, const float* bias,
+                 const float* mask, const float* res, float* out, int B, int H, int W, bool relu,
+                 cudaStream_t s)
+{
+    const dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, B);
+    const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cin * 9 * cout);
+    if (cout == kWide) {
+        cudaFuncSetAttribute(conv3x3_kernel<kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        conv3x3_kernel<kWide><<<grid, kCThreads, smem, s>>>(x, cin, w, tw, bias, mask, res, out, H, W, relu);
+    } else {
+        conv3x3_kernel<1><<<grid, kCThreads, smem, s>>>(x, cin, w, tw, bias, mask, res, out, H, W, relu);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad(int l, const float* x, const float* g, const float* gmask, float* gw, float* gb, int B,
+                  int H, int W, cudaStream_t s)
+{
+    const dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, B);
+    const int cin = cin_of(l), cout = cout_of(l);
+    const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cout * kTile * kTile);
+    if (cin == 1) {
+        conv3x3_wgrad_kernel<1, kWide><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
+    } else if (cout == 1) {
+        conv3x3_wgrad_kernel<kWide, 1><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
+    } else {
+        cudaFuncSetAttribute(conv3x3_wgrad_kernel<kWide, kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        conv3x3_wgrad_kernel<kWide, kWide><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
+    }
+    return cudaGetLastError();
+}
+
+float* hidden(mci_corrector_t c, int l, int64_t pix) { return c->act + (int64_t)l * kWide * pix; }
+
+// forward: hidden activations 0..3, prediction into pred
+cudaError_t forward(mci_corrector_t c, const float* mci, float* pred, int B, int H, int W, cudaStream_t s)
+{
+    const int64_t pix = (int64_t)B * H * W;
+    const float* x = mci;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+        const bool last = l == kLayers - 1;
+        float* y = last ? pred : hidden(c, l, pix);
+        e = conv(x, cin_of(l), cout_of(l), c->wbf + c->woff[l], false, c->master + c->boff[l], nullptr,
+                 last ? mci : nullptr, y, B, H, W, !last, s);
+        x = y;
+    }
+    return e;
+}
+
+// backward from d pred (in gbuf[0] region as [B][1][H][W]); parameter gradients into grad
+cudaError_t backward(mci_corrector_t c, const float* mci, const float* gpred, int B, int H, int W,
+                     cudaStream_t s)
+{
+    const int64_t pix = (int64_t)B * H * W;
+    cudaError_t e = cudaMemsetAsync(c->grad, 0, sizeof(float) * c->n_params, s);
+    const float* g = gpred;         // gradient w.r.t. layer l's output (pre-mask for hidden layers)
+    int gi = 0;
+    for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+        const float* x = l == 0 ? mci : hidden(c, l - 1, pix);
+        const float* gmask = l == kLayers - 1 ? nullptr : hidden(c, l, pix);   // ReLU of this layer
+        e = wgrad(l, x, g, gmask, c->grad + c->woff[l], c->grad + c->boff[l], B, H, W, s);
+        if (l > 0 && e == cudaSuccess) {
+            // gradient w.r.t. layer l's input = hidden(l - 1): conv with transposed, reversed weights
+            float* gin = c->gbuf[gi];
+            e = conv(g, cout_of(l), cin_of(l), c->wbf + c->woff[l], true, nullptr, gmask, nullptr, gin, B, H,
+                     W, false, s);
+            g = gin;
+            gi ^= 1;
+        }
+    }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+mci_status mci_corrector_create(mci_corrector_t* out, int64_t max_pixels, const float* init_params,
+                                mci_stream_t stream)
+{
+    if (!out || max_pixels <= 0) return MCI_ERR_INVALID_ARG;
+    *out = nullptr;
+    mci_corrector_s* c = new (std::nothrow) mci_corrector_s();
+    if (!c) return MCI_ERR_OOM;
+    c->max_pixels = max_pixels;
+    c->n_params = corrector_param_layout(c->woff, c->boff);
+    const int n = c->n_params;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc(&c->master, sizeof(float) * n * 4);
+    if (e == cudaSuccess) {
+        c->grad = c->master + n;
+        c->m1 = c->master + 2 * n;
+        c->m2 = c->master + 3 * n;
+        e = cudaMalloc(&c->wbf, sizeof(__nv_bfloat16) * n);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->act, sizeof(float) * max_pixels * (kWide * (kLayers - 1)));
+    if (e == cudaSuccess) e = cudaMalloc(&c->gbuf[0], sizeof(float) * max_pixels * kWide * 2);
+    if (e == cudaSuccess) c->gbuf[1] = c->gbuf[0] + max_pixels * kWide;
+    if (e == cudaSuccess) e = cudaMalloc(&c->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->master, 0, sizeof(float) * n * 4, s);
+    if (e == cudaSuccess && init_params)
+        e = cudaMemcpyAsync(c->master, init_params, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        to_bf16_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->master, c->wbf, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        mci_corrector_destroy(c);
+        return e == cudaErrorMemoryAllocation ? MCI_ERR_OOM : MCI_ERR_CUDA;
+    }
+    *out = c;
+    return MCI_OK;
+}
+
+int mci_corrector_num_params(void)
+{
+    int wo[kLayers], bo[kLayers];
+    return corrector_param_layout(wo, bo);
+}
+
+mci_status mci_corrector_destroy(mci_corrector_t c)
+{
+    if (!c) return MCI_OK;
+    cudaDeviceSynchronize();
+    cudaFree(c->master);
+    cudaFree(c->wbf);
+    cudaFree(c->act);
+    cudaFree(c->gbuf[0]);
+    cudaFree(c->loss);
+    delete c;
+    return MCI_OK;
+}
+
+mci_status mci_corrector_forward(mci_corrector_t c, const float* mci, float* out, int batch, int h, int w,
+                                 mci_stream_t stream)
+{
+    if (!c || !mci || !out || batch <= 0 || h < 3 || w < 3) return MCI_ERR_INVALID_ARG;
+    if ((int64_t)batch * h * w > c->max_pixels) return MCI_ERR_UNSUPPORTED_SIZE;
+    return forward(c, mci, out, batch, h, w, (cudaStream_t)stream) == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_corrector_loss_grad(mci_corrector_t c, const float* mci, const float* hr, int batch, int h,
+                                   int w, float* grad_out, float* loss_out, mci_stream_t stream)
+{
+    if (!c || !mci || !hr || batch <= 0 || h < 3 || w < 3) return MCI_ERR_INVALID_ARG;
+    const int64_t pix = (int64_t)batch * h * w;
+    if (pix > c->max_pixels) return MCI_ERR_UNSUPPORTED_SIZE;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* pred = c->gbuf[1];        // reused: the first data gradient goes to gbuf[0]
+    float* gpred = c->gbuf[1] + pix;
+    cudaError_t e = forward(c, mci, pred, batch, h, w, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->loss, 0, sizeof(float), s);
+    if (e == cudaSuccess) {
+        mse_kernel<<<304, 256, 0, s>>>(pred, hr, gpred, c->loss, pix);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = backward(c, mci, gpred, batch, h, w, s);
+    if (e == cudaSuccess && grad_out)
+        e = cudaMemcpyAsync(grad_out, c->grad, sizeof(float) * c->n_params, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && loss_out)
+        e = cudaMemcpyAsync(loss_out, c->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_corrector_train_step(mci_corrector_t c, const float* mci, const float* hr, int batch, int h,
+                                    int w, float lr, float* loss_out, mci_stream_t stream)
+{
+    mci_status st = mci_corrector_loss_grad(c, mci, hr, batch, h, w, nullptr, loss_out, stream);
+    if (st != MCI_OK) return st;
+    const float b1 = 0.9f, b2 = 0.999f;
+    c->step += 1;
+    const float c1 = 1.f - std::pow(b1, (float)c->step), c2 = 1.f - std::pow(b2, (float)c->step);
+    adam_kernel<<<(c->n_params + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+        c->master, c->wbf, c->grad, c->m1, c->m2, c->n_params, lr, b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_corrector_get_state(mci_corrector_t c, float* host, int* step)
+{
+    if (!c || !host) return MCI_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host, c->master, sizeof(float) * c->n_params, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(host + c->n_params, c->m1, sizeof(float) * 2 * c->n_params, cudaMemcpyDeviceToHost);
+    if (step) *step = c->step;
+    return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_corrector_set_state(mci_corrector_t c, const float* host, int step)
+{
+    if (!c || !host || step < 0) return MCI_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c->master, host, sizeof(float) * c->n_params, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->m1, host + c->n_params, sizeof(float) * 2 * c->n_params, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        to_bf16_kernel<<<(c->n_params + 255) / 256, 256>>>(c->master, c->wbf, c->n_params);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    c->step = step;
+    return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_generate_images(const float* params, float* img, int n, int h, int w, mci_stream_t stream)
+{
+    if (!params || !img || n <= 0 || h <= 0 || w <= 0) return MCI_ERR_INVALID_ARG;
+    const dim3 blk(32, 8), grid((w + 31) / 32, (h + 7) / 8, n);
+    image_gen_kernel<<<grid, blk, 0, (cudaStream_t)stream>>>(params, img, h, w);
+    return cudaGetLastError() == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_decimate(const float* hr, float* lr, int n, int h, int w, int s, mci_stream_t stream)
+{
+    if (!hr || !lr || n <= 0 || s <= 0 || h % s || w % s) return MCI_ERR_INVALID_ARG;
+    const dim3 blk(32, 8), grid((w / s + 31) / 32, (h / s + 7) / 8, n);
+    decimate_kernel<<<grid, blk, 0, (cudaStream_t)stream>>>(hr, lr, h, w, s);
+    return cudaGetLastError() == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -107,10 +107,18 @@ def load(path: str = LIB_PATH):
         return lib
 
 
-def header_functions(path: str = HEADER):
-    """Names of the functions include/mci.h declares."""
-    text = open(path).read()
-    return sorted(set(re.findall(r"^\s*(?:mci_status|const char\*)\s+(mci_\w+)\s*\(", text, re.M)))
+def header_functions(paths=None):
+    """Names of the functions the headers under include/ declare."""
+    if paths is None:
+        d = os.path.dirname(HEADER)
+        paths = [os.path.join(d, f) for f in sorted(os.listdir(d)) if f.endswith(".h")]
+    elif isinstance(paths, str):
+        paths = [paths]
+    names = set()
+    for path in paths:
+        text = open(path).read()
+        names |= set(re.findall(r"^\s*(?:mci_status|const char\*|int)\s+(mci_\w+)\s*\(", text, re.M))
+    return sorted(names)
 
 
 def error_string(status: int) -> str:

@@ -235,3 +235,26 @@ def synthetic_image(rng, H, W=None):
 def decimate(img, s):
     """Pure decimation: LR pixel p is HR pixel s p (no blur, offset 0)."""
     return np.ascontiguousarray(np.asarray(img)[..., ::s, ::s])
+
+
+def image_params(rng, n, size):
+    """Parameters of n synthetic size x size images for the device generator (192 floats per
+    image): 20 blobs (cy, cx, 1/s_major, 1/s_minor, angle, amp) with s_major ~ U(size/64, size/8),
+    aspect ~ U(1, 4), amp ~ U(-0.4, 0.4); 10 edges (py, px, angle, step +-U(0.1, 0.3));
+    8 waves (cycles_y, cycles_x ~ U{-12..12}, phase, amplitude 0.01)."""
+    out = np.zeros((n, 192), np.float32)
+    for i in range(n):
+        q = out[i]
+        for k in range(20):
+            sm = rng.uniform(size / 64, size / 8)
+            sn = sm / rng.uniform(1, 4)
+            q[6 * k:6 * k + 6] = [rng.uniform(0, size), rng.uniform(0, size), 1 / sm, 1 / sn,
+                                  rng.uniform(0, np.pi), rng.uniform(-0.4, 0.4)]
+        for k in range(10):
+            q[120 + 4 * k:124 + 4 * k] = [rng.uniform(0, size), rng.uniform(0, size),
+                                          rng.uniform(0, np.pi),
+                                          rng.uniform(0.1, 0.3) * rng.choice([-1.0, 1.0])]
+        for k in range(8):
+            q[160 + 4 * k:164 + 4 * k] = [rng.integers(-12, 13), rng.integers(-12, 13),
+                                          rng.uniform(0, 2 * np.pi), 0.01]
+    return out

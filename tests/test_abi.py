@@ -2,6 +2,8 @@
 host-side argument validation (no GPU needed)."""
 import ctypes
 
+import numpy as np
+
 import pytest
 
 from paper_1802_10291_gb300 import mci
@@ -10,7 +12,11 @@ from paper_1802_10291_gb300 import mci
 def test_exports_every_declared_symbol(mci_lib):
     declared = mci.header_functions()
     assert set(declared) == {"mci_plan", "mci_interp_1d", "mci_upsample_2d", "mci_plan_info",
-                             "mci_destroy", "mci_error_string", "mci_interp_1d_noalloc"}
+                             "mci_destroy", "mci_error_string", "mci_interp_1d_noalloc",
+                             "mci_corrector_num_params", "mci_corrector_create", "mci_corrector_forward",
+                             "mci_corrector_loss_grad", "mci_corrector_train_step",
+                             "mci_corrector_get_state", "mci_corrector_set_state",
+                             "mci_corrector_destroy", "mci_generate_images", "mci_decimate"}
     for name in declared:
         assert hasattr(mci_lib, name), name
 
@@ -53,6 +59,19 @@ def test_null_arguments(mci_lib):
         mci.MCI_ERR_INVALID_ARG
     assert mci_lib.mci_plan_info(None, None) == mci.MCI_ERR_INVALID_ARG
     assert mci_lib.mci_destroy(None) == mci.MCI_OK
+
+
+def test_corrector_host_checks(mci_lib):
+    from paper_1802_10291_gb300 import corrector
+    from oracle import corrector as oc
+    assert corrector.num_params() == oc.flatten(oc.unflatten(np.zeros(28353))).size == 28353
+    assert mci_lib.mci_corrector_create(None, 16, None, None) == mci.MCI_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert mci_lib.mci_corrector_create(ctypes.byref(h), 0, None, None) == mci.MCI_ERR_INVALID_ARG
+    assert mci_lib.mci_corrector_forward(None, None, None, 1, 8, 8, None) == mci.MCI_ERR_INVALID_ARG
+    assert mci_lib.mci_corrector_destroy(None) == mci.MCI_OK
+    assert mci_lib.mci_decimate(None, None, 1, 8, 8, 3, None) == mci.MCI_ERR_INVALID_ARG
+    assert mci_lib.mci_generate_images(None, None, 1, 8, 8, None) == mci.MCI_ERR_INVALID_ARG
 
 
 def test_product_refuses_without_library(tmp_path):
