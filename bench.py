@@ -262,6 +262,64 @@ def images_2d_section(mci, torch, dev, timed, steps):
     return out
 
 
+def corrector_section(torch, dev, timed, train_steps=300):
+    """Residual corrector on x4 MCI reconstructions of synthetic 1024^2 images: inference on
+    a batch of 32, training steps on batches of 4 pairs generated on the fly (HR generated on
+    the device, decimated, upsampled by MCI), PSNR of plain MCI and of the trained corrector
+    on 32 held-out images."""
+    from paper_1802_10291_gb300 import corrector
+    size, s_, n_inf, n_tr = 1024, 4, 32, 4
+    out = {}
+    held = corrector.PairSource(n_inf, size, s=s_, seed=1000)
+    xv, hv = held.next()
+    net = corrector.Corrector(n_inf * size * size, corrector.init_params(0))
+    y = torch.empty_like(xv)
+    px = n_inf * size * size
+    t, _ = timed(lambda: net.forward(xv, y, n_inf, size, size), 3, 1)
+    ms = 1e3 * t / 3
+    flop = 2 * 9 * (32 + 3 * 32 * 32 + 32) * px
+    out["inference"] = {"batch": f"{n_inf}x{size}x{size}", "ms_per_batch": ms,
+                        "mpixel_s": px / (ms / 1e3) / 1e6,
+                        "tflop_s": flop / (ms / 1e3) / 1e12, "flop_per_batch": flop}
+    src = corrector.PairSource(n_tr, size, s=s_, seed=1)
+    x, hr = src.next()
+    steps_per_batch = 2
+    t, _ = timed(lambda: net.train_step(x, hr, n_tr, size, size, 1e-3), 5, 1)
+    ms_tr = 1e3 * t / 5
+    t_gen, _ = timed(src.next, 3, 1)
+    ms_gen = 1e3 * t_gen / 3
+    # bounded training from the identity start (last layer zero), then held-out PSNR
+    net.close()
+    net = corrector.Corrector(n_tr * size * size, corrector.init_params(0))
+    torch.cuda.synchronize()
+    t0 = time.time()
+    L = torch.empty(1, device=dev)
+    for it in range(train_steps):
+        if it % steps_per_batch == 0:
+            x, hr = src.next()
+        net.train_step(x, hr, n_tr, size, size, 1e-3, loss=L)
+    torch.cuda.synchronize()
+    wall = time.time() - t0
+    y2 = torch.empty_like(xv[:n_tr])
+    psnr_c = []
+    for i in range(0, n_inf, n_tr):
+        net.forward(xv[i:i + n_tr], y2, n_tr, size, size)
+        psnr_c.append(corrector.psnr(y2, hv[i:i + n_tr]))
+    base = corrector.psnr(xv, hv)
+    got = float(np.mean(psnr_c))
+    pairs = train_steps * n_tr // steps_per_batch
+    out["training"] = {"batch": f"{n_tr}x{size}x{size}", "ms_per_step": ms_tr,
+                       "pair_generation_ms_per_batch": ms_gen,
+                       "train_pairs_s": n_tr / ((ms_tr + ms_gen / steps_per_batch) / 1e3),
+                       "steps": train_steps, "distinct_pairs": pairs, "lr": 1e-3, "wall_s": wall,
+                       "final_loss": float(L.item())}
+    out["psnr_held_out_32"] = {"mci_db": base, "corrected_db": got, "gain_db": got - base}
+    net.close()
+    held.plan.close()
+    src.plan.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -271,7 +329,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="only the FP32 step (for launch lists under a profiler)")
-    ap.add_argument("--case", default=None, choices=["kernel4096"],
+    ap.add_argument("--no-corrector", action="store_true")
+    ap.add_argument("--case", default=None,
+                    choices=["kernel4096", "corrector", "corrector_small", "sisr_s4"],
                     help="profiling case: the P=4096 size-class kernel alone on 3277 signals")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -304,11 +364,12 @@ def main():
     def step(plan, x, y, sc):
         mci.mci_interp_1d(plan.handle, x, None, y, None, sc, N_SIGNALS, stream)
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, collective=True):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
-        barrier(world)
+        if collective:
+            barrier(world)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
@@ -317,9 +378,14 @@ def main():
                 fn()
             e1.record(stream)
             torch.cuda.synchronize()
-        barrier(world)
+        if collective:
+            barrier(world)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, clk.summary()
+
+    def timed_local(fn, steps, warmup):
+        """Rank-local timing for the sections only rank 0 runs."""
+        return timed(fn, steps, warmup, collective=False)
 
     if args.case == "kernel4096":
         sel = np.nonzero(batch["P"] == 4096)[0]
@@ -329,6 +395,38 @@ def main():
         s4, _ = timed(lambda: plan4.interp_1d(g4, y4), args.steps, args.warmup)
         print(json.dumps({"case": args.case, "signals": int(sel.size),
                           "ms_per_launch": 1e3 * s4 / args.steps}), flush=True)
+        return
+
+    if args.case == "corrector_small":
+        # profiling case: forward and training steps of the corrector on 4 x 512^2 pairs
+        from paper_1802_10291_gb300 import corrector
+        src = corrector.PairSource(4, 512, s=4, seed=7)
+        x, hr = src.next()
+        net = corrector.Corrector(4 * 512 * 512, corrector.init_params(0))
+        y = torch.empty_like(x)
+        tf, _ = timed(lambda: net.forward(x, y, 4, 512, 512), args.steps, args.warmup)
+        tt, _ = timed(lambda: net.train_step(x, hr, 4, 512, 512, 1e-3), args.steps, args.warmup)
+        print(json.dumps({"case": args.case, "forward_ms": 1e3 * tf / args.steps,
+                          "train_step_ms": 1e3 * tt / args.steps}), flush=True)
+        return
+    if args.case == "sisr_s4":
+        # profiling case: 64 synthetic 512^2 images from x4 decimation (tensor-core path)
+        from paper_1802_10291_gb300 import synth
+        rng = synth.rng_for(2, 0)
+        hr_np = np.stack([synth.synthetic_image(rng, 512) for _ in range(64)]).astype(np.float32)
+        lr_np = synth.decimate(hr_np, 4)
+        plan = mci.Plan([("identity",), ("deriv", 1)], 128, 512, channels="fd", max_batch=1,
+                        max_images=64, max_intermediate=64 * 128 * 512)
+        lr = torch.tensor(lr_np.reshape(-1), device=dev)
+        hr = torch.empty(64 * 512 * 512, device=dev)
+        hh = np.full(64, 128, np.int32)
+        ss = np.full(64, 4, np.int32)
+        t, _ = timed(lambda: plan.upsample_2d(lr, hh, hh, ss, hr, 64), args.steps, args.warmup)
+        print(json.dumps({"case": args.case, "ms_per_batch": 1e3 * t / args.steps}), flush=True)
+        return
+    if args.case == "corrector":
+        print(json.dumps({"case": args.case, **corrector_section(torch, dev, timed, args.steps)}),
+              flush=True)
         return
 
     # ---- FP32 headline (size classes in host memory: grouped and launched from the host)
@@ -368,7 +466,8 @@ def main():
     k_achieved = k_bytes / (k_ms / 1e3) / 1e9
 
     # ---- image workloads (2-D)
-    images = images_2d_section(mci, torch, dev, timed, args.steps) if rank == 0 else None
+    images = images_2d_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
+    corr = corrector_section(torch, dev, timed_local) if rank == 0 and not args.no_corrector else None
 
     # ---- FP64 on the same batch
     plan64, x64, y64, _ = setup("fp64")
@@ -429,7 +528,7 @@ def main():
                              % (4 * batch["n_in"] / 1e6, 4 * batch["n_out"] / 1e6),
                        "parallelism": f"independent signals per GPU x{world}"},
             "clocks": clocks,
-            "gpu_launches": (1 + n_cls) * args.steps,
+            "gpu_launches": n_cls * args.steps,
             "roofline": {"bound": "hbm", "achieved": k_achieved, "peak": hbm, "unit": "GB/s",
                          "frac": k_achieved / hbm, "traffic": None,
                          "kernel": "mci_kernel<float, N=2048> (P=4096 tiles), timed alone",
@@ -444,6 +543,7 @@ def main():
                      "speedup_fp32_over_fp64": value / value64},
             "err_vs_oracle": err,
             "images_2d": images,
+            "corrector": corr,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * batch["n_in"] + plan32_stage_bytes,
                     "d2h_bytes_per_step": 4 * batch["n_out"]},

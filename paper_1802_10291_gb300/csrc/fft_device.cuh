@@ -178,8 +178,6 @@ __device__ __forceinline__ void dft(cpx<R>* v)
 // pass last).  Because the radix-3 pass comes last, every Ns before it is a
 // power of two, so all index arithmetic is shifts and masks.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int ilog2(int x) { return 31 - __clz(x); }
-
 // Returns x through an opaque move, so index arithmetic derived from it is
 // recomputed where it is used instead of being hoisted out of loops and kept
 // live in registers across them.
@@ -196,24 +194,42 @@ __device__ __forceinline__ int opaque(int x)
 // kernel spill).
 __device__ __forceinline__ int ltid() { return opaque((int)threadIdx.x); }
 
+// Padded shared-memory positions of a butterfly: when the offsets pad16(x + c_r) -
+// pad16(x) of a pass's R reads (or writes) do not depend on the butterfly's base x,
+// they are compile-time constants and every access is base + immediate.
+//   reads  x = j (< N / RAD), c_r = r * N / RAD: constant when N / RAD is a multiple of
+//          32 or a power of two (no carry into bit 5 from the low part);
+//   writes x = (j div NS) NS RAD + j mod NS, c_r = r * NS: constant when NS is a power of
+//          two and NS >= 32, or NS * RAD divides 32, or 32 divides NS * RAD.
+__host__ __device__ constexpr bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+__host__ __device__ constexpr bool read_offsets_const(int N, int RAD)
+{
+    return (N / RAD) % 32 == 0 || is_pow2(N / RAD);
+}
+__host__ __device__ constexpr bool write_offsets_const(int NS, int RAD)
+{
+    return is_pow2(NS) && (NS >= 32 || 32 % (NS * RAD) == 0 || (NS * RAD) % 32 == 0);
+}
+
 // One Stockham pass of radix RAD over nfft length-N buffers (buffer f at
 // sm + base_of(f)); E elements per thread, groups of N/E threads per buffer.
 // Butterfly j needs w^r, r < RAD, w = e^{-2 pi i (j mod NS) / (NS RAD)}: w is read
 // from this pass's shared-memory twiddle row stw (built at tile start), its
 // powers come from a product tree of depth <= 4.  With GIN the pass reads its
 // input from global memory (src_of(f), natural order, first pass only).
-template <typename R, int E, int RAD, bool INV, bool GIN, typename BaseFn, typename SrcFn>
-__device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int N, int NS, int nfft, BaseFn base_of,
-                                              SrcFn src_of, const cpx<R>* stw)
+template <typename R, int N, int NS, int E, int RAD, bool INV, bool GIN, typename BaseFn, typename SrcFn>
+__device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int nfft, BaseFn base_of, SrcFn src_of,
+                                              const cpx<R>* stw)
 {
     constexpr int NB = E / RAD;
-    const int TPF = N / E;
+    constexpr int TPF = N / E;
+    constexpr int STRIDE = N / RAD;
+    constexpr bool RD_CONST = read_offsets_const(N, RAD);
+    constexpr bool WR_CONST = write_offsets_const(NS, RAD);
     const int tix = ltid();
     const int groups = blockDim.x / TPF;
     const int gi = tix / TPF;
     const int lt = tix - gi * TPF;
-    const int stride = N / RAD;
-    const int lgNS = ilog2(NS);            // NS is a power of two
 #pragma unroll 1
     for (int f0 = 0; f0 < nfft; f0 += groups) {
         const int f = f0 + gi;
@@ -232,13 +248,19 @@ __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int N, int NS, int nff
 #pragma unroll
                 for (int i = 0; i < NB; ++i)
 #pragma unroll
-                    for (int r = 0; r < RAD; ++r) v[i * RAD + r] = src[ltr + i * TPF + r * stride];
+                    for (int r = 0; r < RAD; ++r) v[i * RAD + r] = src[ltr + i * TPF + r * STRIDE];
             } else {
 #pragma unroll
                 for (int i = 0; i < NB; ++i) {
                     const int j = ltr + i * TPF;
+                    if constexpr (RD_CONST) {
+                        const cpx<R>* b = buf + pad16(j);
 #pragma unroll
-                    for (int r = 0; r < RAD; ++r) v[i * RAD + r] = buf[pad16(j + r * stride)];
+                        for (int r = 0; r < RAD; ++r) v[i * RAD + r] = b[pad16(r * STRIDE)];
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < RAD; ++r) v[i * RAD + r] = buf[pad16(j + r * STRIDE)];
+                    }
                 }
             }
         }
@@ -249,7 +271,7 @@ __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int N, int NS, int nff
             for (int i = 0; i < NB; ++i) {
                 const int j = lts + i * TPF;
                 const int jm = j & (NS - 1);
-                if (NS > 1) {
+                if constexpr (NS > 1) {
                     cpx<R> w[RAD];
                     w[1] = w1[i];
 #pragma unroll
@@ -260,9 +282,15 @@ __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int N, int NS, int nff
                         v[i * RAD + r] = INV ? cmulc(v[i * RAD + r], w[r]) : cmul(v[i * RAD + r], w[r]);
                 }
                 dft<RAD, INV>(&v[i * RAD]);
-                const int d = ((j >> lgNS) << lgNS) * RAD + jm;
+                const int d = (j - jm) * RAD + jm;
+                if constexpr (WR_CONST) {
+                    cpx<R>* b = buf + pad16(d);
 #pragma unroll
-                for (int r = 0; r < RAD; ++r) buf[pad16(d + r * NS)] = v[i * RAD + r];
+                    for (int r = 0; r < RAD; ++r) b[pad16(r * NS)] = v[i * RAD + r];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RAD; ++r) buf[pad16(d + r * NS)] = v[i * RAD + r];
+                }
             }
         }
         __syncthreads();
@@ -282,8 +310,8 @@ __device__ __forceinline__ void fft_passes_ct(cpx<R>* sm, int nfft, BaseFn base_
 {
     if constexpr (NS < N) {
         constexpr int RAD = pick_radix(N / NS, E);
-        fft_pass_many<R, E, RAD, INV, GIN && NS == 1>(sm, N, NS, nfft, base_of, src_of,
-                                                        stw + smem_twiddle_offset(N, NS));
+        fft_pass_many<R, N, NS, E, RAD, INV, GIN && NS == 1>(sm, nfft, base_of, src_of,
+                                                               stw + smem_twiddle_offset(N, NS));
         fft_passes_ct<R, N, E, NS * RAD, INV, GIN>(sm, nfft, base_of, src_of, stw);
     }
 }
@@ -311,6 +339,24 @@ __device__ __forceinline__ cpx<double> cis_neg<double>(int num, int den)
 {
     double s, c;
     sincospi(2.0 * (double)num / (double)den, &s, &c);
+    return {c, -s};
+}
+
+// e^{-pi i x} for x = 2 num / den given as num * (2 / den) (the caller hoists 2 / den)
+template <typename R>
+__device__ __forceinline__ cpx<R> cis_neg_pi(R x);
+template <>
+__device__ __forceinline__ cpx<float> cis_neg_pi<float>(float x)
+{
+    float s, c;
+    sincospif(x, &s, &c);
+    return {c, -s};
+}
+template <>
+__device__ __forceinline__ cpx<double> cis_neg_pi<double>(double x)
+{
+    double s, c;
+    sincospi(x, &s, &c);
     return {c, -s};
 }
 

@@ -32,6 +32,7 @@ namespace {
 constexpr int kTile = 16;          // output tile edge
 constexpr int kHalo = kTile + 2;   // input tile edge
 constexpr int kCThreads = kTile * kTile;
+constexpr int kGStride = kTile * kTile + 1;   // per-channel stride of the gradient tile (wgrad)
 constexpr int kWide = 32;          // hidden channels
 constexpr int kLayers = 5;
 __host__ __device__ constexpr int cin_of(int l) { return l == 0 ? 1 : kWide; }
@@ -124,7 +125,8 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_wgrad_kernel(
 {
     extern __shared__ float csm[];
     float* xs = csm;                          // [CIN][18][18]
-    float* gs = csm + CIN * kHalo * kHalo;    // [COUT][16][16]
+    float* gs = csm + CIN * kHalo * kHalo;    // [COUT][16 * 16 + 1]: odd channel stride, so the
+                                              // lanes of a warp (different co) hit different banks
     const int b = blockIdx.z;
     const int y0 = blockIdx.y * kTile, x0 = blockIdx.x * kTile;
     const int tid = threadIdx.x;
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_wgrad_kernel(
             v = g[gi];
             if (gmask && !(gmask[gi] > 0.f)) v = 0.f;
         }
-        gs[i] = v;
+        gs[co * kGStride + r] = v;
     }
     __syncthreads();
     constexpr int PAIRS = CIN * COUT;                     // (co, ci) pairs
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_wgrad_kernel(
             float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             float accb = 0.f;
             const float* xc = xs + ci * kHalo * kHalo;
-            const float* gc = gs + co * kTile * kTile;
+            const float* gc = gs + co * kGStride;
             for (int p = 0; p < kTile * kTile; ++p) {
                 const float gv = gc[p];
                 const int py = p / kTile, px = p % kTile;
@@ -308,7 +310,7 @@ cudaError_t wgrad(int l, const float* x, const float* g, const float* gmask, flo
 {
     const dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, B);
     const int cin = cin_of(l), cout = cout_of(l);
-    const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cout * kTile * kTile);
+    const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cout * kGStride);
     if (cin == 1) {
         conv3x3_wgrad_kernel<1, kWide><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
     } else if (cout == 1) {

@@ -710,6 +710,9 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         cd_.Q = hc.s * p->n_out;
         cd_.QM = std::max(cd_.M_in, cd_.Q);
         cd_.npad = padded_len(hc.N);
+        cd_.mag_min = fastdiv_magic(cd_.M_in);
+        cd_.mag_q = fastdiv_magic(cd_.Q);
+        cd_.mag_nout = fastdiv_magic(cd_.n_out);
         const int per = cd_.QM * cd_.npad * csz + smem_twiddle_count(hc.N) * csz;
         if (per > smem_cap) {
             delete p;

@@ -22,6 +22,11 @@ constexpr int kSmemBudget = 64 * 1024;  // preferred dynamic shared memory per C
 // complex of padding after every 32 keep strided Stockham stores free of bank
 // conflicts and keep even elements 16-byte aligned (vector loads of pairs).
 MCI_HD constexpr int pad16(int e) { return e + 2 * (e >> 5); }
+
+// Division by a small runtime divisor d without a divide: n / d = (n * m) >> 32 with
+// m = ceil(2^32 / d), exact for 0 <= n with n * d < 2^32 (buffer and item indices of a tile).
+MCI_HD constexpr uint64_t fastdiv_magic(int d) { return ((1ull << 32) + (uint64_t)d - 1) / (uint64_t)d; }
+MCI_HD inline int fastdiv(int n, uint64_t m) { return (int)(((uint64_t)(unsigned)n * m) >> 32); }
 MCI_HD constexpr int padded_len(int n) { return ((pad16(n) + 1) / 2) * 2; }
 
 // Radix plan of a length-n FFT, shared by the host (twiddle tables) and the
@@ -68,6 +73,7 @@ struct ClassDev {
     int n_out;   // outputs per signal
     int npad;    // padded FFT buffer length (complex elements)
     int64_t w_off;   // offset of this class's bin weights W[k][m][q], k = 0..N
+    uint64_t mag_min, mag_q, mag_nout;   // fastdiv_magic of M_in, Q and n_out
 };
 
 // Device-built grouping of one mci_interp_1d call (uneven batches).

@@ -71,7 +71,7 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
             __syncthreads();
             compute_tile<R, N>(sm, c, cnt, W);
         }
-        store_contig<R>(sm, c, static_cast<R*>(a.out), s_out, cnt);
+        store_contig<R, N>(sm, c, static_cast<R*>(a.out), s_out, cnt);
         __syncthreads();
     }
 }

@@ -41,12 +41,16 @@ __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int 
     const int npad = c.npad, QM = c.QM, Min = c.M_in, Q = c.Q, N = c.N;
     const int NH = N / 2;
     const int total = (NH + 1) * gcount;
-    for (int it = ltid(); it < total; it += blockDim.x) {
-        const int g = it % gcount;
-        const int k = it / gcount;
+    const R two_over_p = R(2) / R(c.P);
+    // item it = k * gcount + g; (k, g) advance incrementally (no division in the loop)
+    const int it0 = ltid();
+    const int step = blockDim.x;
+    const int dk = step / gcount, dg = step - dk * gcount;
+    int k = it0 / gcount, g = it0 - k * gcount;
+    for (int it = it0; it < total; it += step) {
         const int kk = (N - k) % N;  // mirror bin (k = 0 pairs with bin N == 0 of Z)
         cpx<R>* base = sm + g * QM * npad;
-        const cpx<R> w = cis_neg<R>(k, c.P);  // e^{-2 pi i k / P}
+        const cpx<R> w = cis_neg_pi<R>(R(k) * two_over_p);  // e^{-2 pi i k / P}
         cpx<R> Xa[MCI_MAX_CHANNELS], Xb[MCI_MAX_CHANNELS];
 #pragma unroll
         for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
@@ -107,15 +111,22 @@ __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int 
             }
             emit(q, ya, yb);
         }
+        k += dk;
+        g += dg;
+        if (g >= gcount) {
+            g -= gcount;
+            ++k;
+        }
     }
 }
 
 // Buffer f of a tile with `cnt` transforms per signal: signal f / cnt, slot f % cnt.
 struct SlotBase {
     int cnt, QM, npad;
+    uint64_t mag;   // fastdiv_magic(cnt)
     __device__ __forceinline__ int operator()(int f) const
     {
-        const int g = f / cnt;
+        const int g = fastdiv(f, mag);
         return (g * QM + (f - g * cnt)) * npad;
     }
 };
@@ -127,9 +138,10 @@ struct SrcContig {
     const R* in;
     const int64_t* off;
     int Min, P;
+    uint64_t mag;   // fastdiv_magic(Min)
     __device__ __forceinline__ const cpx<R>* operator()(int f) const
     {
-        const int g = f / Min;
+        const int g = fastdiv(f, mag);
         return reinterpret_cast<const cpx<R>*>(in + off[g] + (int64_t)(f - g * Min) * P);
     }
 };
@@ -146,13 +158,13 @@ __device__ __forceinline__ void compute_tile(cpx<R>* sm, const ClassDev& c, int 
     cpx<R>* stw = sm + c.G * c.QM * c.npad;
     fill_twiddles_ct<R, N, elems_per_thread(N), 1>(stw);
     if (gin)
-        fft_many_ct<R, N, false, true>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad}, stw,
-                                       SrcContig<R>{gin, s_in, c.M_in, c.P});
+        fft_many_ct<R, N, false, true>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad, c.mag_min}, stw,
+                                       SrcContig<R>{gin, s_in, c.M_in, c.P, c.mag_min});
     else
-        fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad}, stw);
+        fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad, c.mag_min}, stw);
     combine_tile<R>(sm, c, gcount, W);
     __syncthreads();
-    fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.QM, c.npad}, stw);
+    fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.QM, c.npad, c.mag_q}, stw);
 }
 
 // ---------------------------------------------------------------------------
@@ -201,51 +213,56 @@ __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const
     }
 }
 
-// Contiguous outputs: output o of signal g at out + off[g] + o * T, T = s P samples;
-// sample j = s * (2l + e) + u is component e of phase (o, u) at position l.  Threads
-// run over (signal, vector) pairs of the whole tile.
-template <typename R>
+// Contiguous outputs: output o of signal g at out + off[g] + o * T, T = s P samples.
+// Complex element l of phase buffer (o, u) holds samples s (2l) + u (real part) and
+// s (2l + 1) + u (imaginary part), so one thread per (g, o, l) gathers the s phases
+// and writes the 2s consecutive samples [2ls, 2ls + 2s): consecutive threads write
+// consecutive runs.  Runs are written as 16-byte vectors when s is even (FP64) or a
+// multiple of 4 (FP32) and the outputs are 16-byte aligned, as 8-byte pairs for
+// FP32 with s even, else as scalars.
+template <typename R, int N>
 __device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
                                              const int64_t* off, int gcount)
 {
     const int T = c.T, s = c.s, npad = c.npad, QM = c.QM, nout = c.n_out;
-    const int per = nout * T;
-    bool vec = (T % 4) == 0;
-    for (int g = 0; g < gcount; ++g) vec = vec && ((reinterpret_cast<uintptr_t>(out + off[g]) & 15) == 0);
-    if (vec) {
-        const int nv = per / 4;
-        for (int t = ltid(); t < gcount * nv; t += blockDim.x) {
-            const int g = t / nv, v = t - g * nv;
-            const cpx<R>* srcs = sm + g * QM * npad;
-            R* dst = out + off[g];
-            const int i0 = v * 4;
-            const int o = i0 / T;
-            const int x0 = i0 - o * T;
-            int l2 = x0 / s, u = x0 - l2 * s;   // sample x = s * l2 + u
-            R val[4];
+    constexpr int VR = 16 / sizeof(R);     // reals per 16-byte vector
+    bool vec = (s % VR) == 0 && (T % VR) == 0, vec2 = sizeof(R) == 4 && (s % 2) == 0;
+    for (int g = 0; g < gcount; ++g) {
+        vec = vec && ((reinterpret_cast<uintptr_t>(out + off[g]) & 15) == 0);
+        vec2 = vec2 && ((reinterpret_cast<uintptr_t>(out + off[g]) & 7) == 0);
+    }
+    const int total = gcount * nout * N;
+    for (int t = ltid(); t < total; t += blockDim.x) {
+        const int go = t / N;                    // compile-time N: shift or multiply
+        const int l = t - go * N;
+        const int g = fastdiv(go, c.mag_nout), o = go - g * nout;
+        const cpx<R>* src = sm + (g * QM + o * s) * npad + pad16(l);
+        R* dst = out + off[g] + (int64_t)o * T + (int64_t)2 * l * s;
+        if (vec) {
+            for (int u = 0; u < s; u += VR) {
+                cpx<R> z[VR];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const cpx<R> z = srcs[(o * s + u) * npad + pad16(l2 >> 1)];
-                val[e] = (l2 & 1) ? z.y : z.x;
-                if (++u == s) {
-                    u = 0;
-                    ++l2;
+                for (int e = 0; e < VR; ++e) z[e] = src[(u + e) * npad];
+                if constexpr (sizeof(R) == 4) {
+                    *reinterpret_cast<float4*>(dst + u) = make_float4(z[0].x, z[1].x, z[2].x, z[3].x);
+                    *reinterpret_cast<float4*>(dst + s + u) = make_float4(z[0].y, z[1].y, z[2].y, z[3].y);
+                } else {
+                    *reinterpret_cast<double2*>(dst + u) = make_double2(z[0].x, z[1].x);
+                    *reinterpret_cast<double2*>(dst + s + u) = make_double2(z[0].y, z[1].y);
                 }
             }
-            if constexpr (sizeof(R) == 4) {
-                reinterpret_cast<float4*>(dst)[v] = make_float4(val[0], val[1], val[2], val[3]);
-            } else {
-                reinterpret_cast<double2*>(dst)[2 * v] = make_double2(val[0], val[1]);
-                reinterpret_cast<double2*>(dst)[2 * v + 1] = make_double2(val[2], val[3]);
+        } else if (vec2) {      // FP32, s even: 8-byte pairs
+            for (int u = 0; u < s; u += 2) {
+                const cpx<R> z0 = src[u * npad], z1 = src[(u + 1) * npad];
+                *reinterpret_cast<float2*>(dst + u) = make_float2(z0.x, z1.x);
+                *reinterpret_cast<float2*>(dst + s + u) = make_float2(z0.y, z1.y);
             }
-        }
-    } else {
-        for (int t = ltid(); t < gcount * per; t += blockDim.x) {
-            const int g = t / per, i = t - g * per;
-            const int o = i / T, x = i - o * T;
-            const int l2 = x / s, u = x - l2 * s;
-            const cpx<R> z = sm[(g * QM + o * s + u) * npad + pad16(l2 >> 1)];
-            out[off[g] + i] = (l2 & 1) ? z.y : z.x;
+        } else {
+            for (int u = 0; u < s; ++u) {
+                const cpx<R> z = src[u * npad];
+                dst[u] = z.x;
+                dst[s + u] = z.y;
+            }
         }
     }
 }
