@@ -352,6 +352,9 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
         const bool gemm = gemm_eligible(p, hc);
         std::vector<cd> w1;  // single-input-channel weights per bin, phase (GEMM matrix)
         if (gemm) w1.assign((size_t)(N + 1) * Q, 0.0);
+        // stored as planes: plane (m, q) holds W[k][m][q] for k = 0..N contiguously, so the
+        // threads of a warp (consecutive bins) read consecutive elements of a plane
+        std::vector<cd> planes((size_t)Min * Q * (N + 1));
         for (int k = 0; k <= N; ++k) {
             const int ra = res(k), rb = res((P - k) % P);
             for (int m = 0; m < M; ++m)
@@ -361,16 +364,17 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
                 for (int q = 0; q < Q; ++q) {
                     cd acc = 0.0;
                     for (int m = 0; m < M; ++m) acc += fd_factor(d.sys[m], P, k) * Wk[(size_t)m * Q + q];
-                    push_cpx(W, acc);
+                    planes[(size_t)q * (N + 1) + k] = acc;
                     if (gemm) w1[(size_t)k * Q + q] = acc;
                 }
             } else {
                 for (int m = 0; m < Min; ++m)
-                    for (int q = 0; q < Q; ++q) push_cpx(W, Wk[(size_t)m * Q + q]);
+                    for (int q = 0; q < Q; ++q) planes[((size_t)m * Q + q) * (N + 1) + k] = Wk[(size_t)m * Q + q];
                 if (gemm)
                     for (int q = 0; q < Q; ++q) w1[(size_t)k * Q + q] = Wk[q];
             }
         }
+        for (const cd& z : planes) push_cpx(W, z);
         if (gemm) {
             // out[s l + u] = sum_p kappa_u[(l - p) mod P] x[p], kappa_u[d] = sum over all P bins of
             // W_k[u] e^{2 pi i k d / P} with W_{P-k} = conj W_k (the kernel's real inverse FFT)

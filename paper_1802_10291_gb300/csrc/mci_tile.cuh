@@ -21,96 +21,121 @@
 
 namespace mci {
 
-// Two consecutive weights (q, q + 1) in one 16-byte load where the type allows.
-__device__ __forceinline__ void ld_w2(const cpx<float>* p, cpx<float>& a, cpx<float>& b)
+// Combine of one bin pair (k, N - k), 0 <= k <= N/2, of one signal (buffers at base):
+// the real-input spectrum X_m of every channel from its packed FFT Z_m, then
+// Y_q = sum_m X_m W_m,q for both bins of the pair and every phase q, packed for the
+// real inverse FFT.  W is stored as planes: W_m,q[k] at W[(m Q + q)(N + 1) + k].
+// MIN, Q > 0 fix the channel and phase counts at compile time (all weight loads of
+// the pair are independent and issued together); MIN = 0 takes them from c.
+// Read-only cached load of one weight.
+__device__ __forceinline__ cpx<float> ldw(const cpx<float>* p)
 {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    a = {v.x, v.y};
-    b = {v.z, v.w};
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
 }
-__device__ __forceinline__ void ld_w2(const cpx<double>* p, cpx<double>& a, cpx<double>& b)
+__device__ __forceinline__ cpx<double> ldw(const cpx<double>* p)
 {
-    a = p[0];
-    b = p[1];
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
 }
 
-template <typename R>
-__device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int gcount,
-                                          const cpx<R>* __restrict__ W)
+template <typename R, int MIN, int QC>
+__device__ __forceinline__ void combine_pair(cpx<R>* base, const ClassDev& c, int k,
+                                             const cpx<R>* __restrict__ W, cpx<R> w)
 {
-    const int npad = c.npad, QM = c.QM, Min = c.M_in, Q = c.Q, N = c.N;
-    const int NH = N / 2;
-    const int total = (NH + 1) * gcount;
+    const int npad = c.npad, N = c.N, NH = N / 2;
+    const int Min = MIN > 0 ? MIN : c.M_in, Q = MIN > 0 ? QC : c.Q;
+    const int ws = N + 1;
+    const int kk = k == 0 ? 0 : N - k;   // mirror bin (k = 0 pairs with bin N == 0 of Z)
+    const int pk = pad16(k), pkk = pad16(kk);
+    // pack: Z'[k] = A + iC, Z'[N-k] = conj(A) + i conj(C),
+    // A = Y[k] + conj Y[N-k], C = e^{2 pi i k / P} (Y[k] - conj Y[N-k])
+    auto emit = [&](int q, cpx<R> ya, cpx<R> yb) {
+        const cpx<R> A = ya + conjc(yb);
+        const cpx<R> C = cmulc(ya - conjc(yb), w);
+        base[q * npad + pk] = mk<R>(A.x - C.y, A.y + C.x);
+        if (k != 0 && k != NH) base[q * npad + pkk] = mk<R>(A.x + C.y, C.x - A.y);
+    };
+    auto spectrum = [&](int m, cpx<R>& xa, cpx<R>& xb) {
+        const cpx<R> zk = base[m * npad + pk];
+        const cpx<R> zn = base[m * npad + pkk];
+        if (k == 0) {
+            xa = mk<R>(zk.x + zk.y, R(0));  // X[0]
+            xb = mk<R>(zk.x - zk.y, R(0));  // X[N]
+        } else {
+            const cpx<R> e = scale(zk + conjc(zn), R(0.5));
+            const cpx<R> d = zk - conjc(zn);
+            const cpx<R> o = mk<R>(R(0.5) * d.y, R(-0.5) * d.x);  // d / (2i)
+            const cpx<R> wo = cmul(w, o);
+            xa = e + wo;                 // X[k]
+            xb = conjc(e - wo);          // X[N-k]
+        }
+    };
+    if constexpr (MIN > 0) {
+        // FP32: every weight of the pair is loaded up front; FP64 (twice the registers):
+        // one channel's weights at a time
+        constexpr int MH = sizeof(R) == 4 ? MIN : 1;
+        cpx<R> wa[MH][QC], wb[MH][QC];
+        auto load = [&](int m, int slot) {
+#pragma unroll
+            for (int q = 0; q < QC; ++q) {
+                wa[slot][q] = ldw(&W[(m * QC + q) * ws + k]);
+                wb[slot][q] = ldw(&W[(m * QC + q) * ws + (N - k)]);
+            }
+        };
+        if constexpr (MH == MIN) {
+#pragma unroll
+            for (int m = 0; m < MIN; ++m) load(m, m);
+        }
+        cpx<R> ya[QC], yb[QC];
+#pragma unroll
+        for (int m = 0; m < MIN; ++m) {
+            const int sl = MH == MIN ? m : 0;
+            if constexpr (MH != MIN) load(m, 0);
+            cpx<R> xa, xb;
+            spectrum(m, xa, xb);
+#pragma unroll
+            for (int q = 0; q < QC; ++q) {
+                ya[q] = m == 0 ? cmul(xa, wa[sl][q]) : ya[q] + cmul(xa, wa[sl][q]);
+                yb[q] = m == 0 ? cmul(xb, wb[sl][q]) : yb[q] + cmul(xb, wb[sl][q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < QC; ++q) emit(q, ya[q], yb[q]);
+    } else {
+        cpx<R> Xa[MCI_MAX_CHANNELS], Xb[MCI_MAX_CHANNELS];
+#pragma unroll
+        for (int m = 0; m < MCI_MAX_CHANNELS; ++m)
+            if (m < Min) spectrum(m, Xa[m], Xb[m]);
+        for (int q = 0; q < Q; ++q) {
+            cpx<R> ya = mk<R>(0, 0), yb = mk<R>(0, 0);
+#pragma unroll
+            for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
+                if (m < Min) {
+                    ya = ya + cmul(Xa[m], ldw(&W[(m * Q + q) * ws + k]));
+                    yb = yb + cmul(Xb[m], ldw(&W[(m * Q + q) * ws + (N - k)]));
+                }
+            }
+            emit(q, ya, yb);
+        }
+    }
+}
+
+template <typename R, int MIN, int QC>
+__device__ __forceinline__ void combine_loop(cpx<R>* sm, const ClassDev& c, int gcount,
+                                             const cpx<R>* __restrict__ W)
+{
+    const int total = (c.N / 2 + 1) * gcount;
     const R two_over_p = R(2) / R(c.P);
+    const int QMn = c.QM * c.npad;
     // item it = k * gcount + g; (k, g) advance incrementally (no division in the loop)
     const int it0 = ltid();
     const int step = blockDim.x;
     const int dk = step / gcount, dg = step - dk * gcount;
     int k = it0 / gcount, g = it0 - k * gcount;
     for (int it = it0; it < total; it += step) {
-        const int kk = (N - k) % N;  // mirror bin (k = 0 pairs with bin N == 0 of Z)
-        cpx<R>* base = sm + g * QM * npad;
         const cpx<R> w = cis_neg_pi<R>(R(k) * two_over_p);  // e^{-2 pi i k / P}
-        cpx<R> Xa[MCI_MAX_CHANNELS], Xb[MCI_MAX_CHANNELS];
-#pragma unroll
-        for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
-            if (m < Min) {
-                const cpx<R> zk = base[m * npad + pad16(k)];
-                const cpx<R> zn = base[m * npad + pad16(kk)];
-                if (k == 0) {
-                    Xa[m] = mk<R>(zk.x + zk.y, R(0));  // X[0]
-                    Xb[m] = mk<R>(zk.x - zk.y, R(0));  // X[N]
-                } else {
-                    const cpx<R> e = scale(zk + conjc(zn), R(0.5));
-                    const cpx<R> d = zk - conjc(zn);
-                    const cpx<R> o = mk<R>(R(0.5) * d.y, R(-0.5) * d.x);  // d / (2i)
-                    const cpx<R> wo = cmul(w, o);
-                    Xa[m] = e + wo;                 // X[k]
-                    Xb[m] = conjc(e - wo);          // X[N-k]
-                }
-            }
-        }
-        const cpx<R>* Wa = W + (int64_t)k * Min * Q;
-        const cpx<R>* Wb = W + (int64_t)(N - k) * Min * Q;
-        // pack: Z'[k] = A + iC, Z'[N-k] = conj(A) + i conj(C),
-        // A = Y[k] + conj Y[N-k], C = e^{2 pi i k / P} (Y[k] - conj Y[N-k])
-        auto emit = [&](int q, cpx<R> ya, cpx<R> yb) {
-            const cpx<R> A = ya + conjc(yb);
-            const cpx<R> C = cmulc(ya - conjc(yb), w);
-            base[q * npad + pad16(k)] = mk<R>(A.x - C.y, A.y + C.x);
-            if (k != 0 && k != NH) base[q * npad + pad16(kk)] = mk<R>(A.x + C.y, C.x - A.y);
-        };
-        int q = 0;
-        if ((Q & 1) == 0) {
-            for (; q < Q; q += 2) {
-                cpx<R> ya0 = mk<R>(0, 0), yb0 = mk<R>(0, 0), ya1 = mk<R>(0, 0), yb1 = mk<R>(0, 0);
-#pragma unroll
-                for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
-                    if (m < Min) {
-                        cpx<R> wa0, wa1, wb0, wb1;
-                        ld_w2(Wa + m * Q + q, wa0, wa1);
-                        ld_w2(Wb + m * Q + q, wb0, wb1);
-                        ya0 = ya0 + cmul(Xa[m], wa0);
-                        ya1 = ya1 + cmul(Xa[m], wa1);
-                        yb0 = yb0 + cmul(Xb[m], wb0);
-                        yb1 = yb1 + cmul(Xb[m], wb1);
-                    }
-                }
-                emit(q, ya0, yb0);
-                emit(q + 1, ya1, yb1);
-            }
-        }
-        for (; q < Q; ++q) {
-            cpx<R> ya = mk<R>(0, 0), yb = mk<R>(0, 0);
-#pragma unroll
-            for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
-                if (m < Min) {
-                    ya = ya + cmul(Xa[m], Wa[m * Q + q]);
-                    yb = yb + cmul(Xb[m], Wb[m * Q + q]);
-                }
-            }
-            emit(q, ya, yb);
-        }
+        combine_pair<R, MIN, QC>(sm + g * QMn, c, k, W, w);
         k += dk;
         g += dg;
         if (g >= gcount) {
@@ -118,6 +143,20 @@ __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int 
             ++k;
         }
     }
+}
+
+// Channel/phase counts with a compile-time combine: M = 3 measured channels with
+// s = 4 phases (batched 1-D), and one channel with s = 2, 3, 4 (image rows and
+// columns with derivative channels formed from the samples).
+template <typename R>
+__device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int gcount,
+                                             const cpx<R>* __restrict__ W)
+{
+    if (c.M_in == 3 && c.Q == 4) combine_loop<R, 3, 4>(sm, c, gcount, W);
+    else if (c.M_in == 1 && c.Q == 2) combine_loop<R, 1, 2>(sm, c, gcount, W);
+    else if (c.M_in == 1 && c.Q == 3) combine_loop<R, 1, 3>(sm, c, gcount, W);
+    else if (c.M_in == 1 && c.Q == 4) combine_loop<R, 1, 4>(sm, c, gcount, W);
+    else combine_loop<R, 0, 0>(sm, c, gcount, W);
 }
 
 // Buffer f of a tile with `cnt` transforms per signal: signal f / cnt, slot f % cnt.
