@@ -216,10 +216,12 @@ __host__ __device__ constexpr bool write_offsets_const(int NS, int RAD)
 // Butterfly j needs w^r, r < RAD, w = e^{-2 pi i (j mod NS) / (NS RAD)}: w is read
 // from this pass's shared-memory twiddle row stw (built at tile start), its
 // powers come from a product tree of depth <= 4.  With GIN the pass reads its
-// input from global memory (src_of(f), natural order, first pass only).
-template <typename R, int N, int NS, int E, int RAD, bool INV, bool GIN, typename BaseFn, typename SrcFn>
+// input from global memory (src_of(f), natural order, first pass only) and runs
+// hook() (all threads, once) while those loads are in flight.
+template <typename R, int N, int NS, int E, int RAD, bool INV, bool GIN, typename BaseFn, typename SrcFn,
+          typename Hook>
 __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int nfft, BaseFn base_of, SrcFn src_of,
-                                              const cpx<R>* stw)
+                                              const cpx<R>* stw, Hook hook)
 {
     constexpr int NB = E / RAD;
     constexpr int TPF = N / E;
@@ -265,6 +267,9 @@ __device__ __forceinline__ void fft_pass_many(cpx<R>* sm, int nfft, BaseFn base_
             }
         }
         if constexpr (!GIN) __syncthreads();
+        if constexpr (GIN) {
+            if (f0 == 0) hook();
+        }
         if (active) {
             const int lts = opaque(lt);
 #pragma unroll
@@ -302,26 +307,32 @@ struct NoSrc {
     __device__ __forceinline__ const T* operator()(int) const { return nullptr; }
 };
 
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // Compile-time radix sequence of a length-N transform with E elements per thread
 // (pick_radix); stw is the shared-memory twiddle table (smem_twiddle_offset).
-template <typename R, int N, int E, int NS, bool INV, bool GIN, typename BaseFn, typename SrcFn>
+template <typename R, int N, int E, int NS, bool INV, bool GIN, typename BaseFn, typename SrcFn,
+          typename Hook>
 __device__ __forceinline__ void fft_passes_ct(cpx<R>* sm, int nfft, BaseFn base_of, SrcFn src_of,
-                                              const cpx<R>* stw)
+                                              const cpx<R>* stw, Hook hook)
 {
     if constexpr (NS < N) {
         constexpr int RAD = pick_radix(N / NS, E);
         fft_pass_many<R, N, NS, E, RAD, INV, GIN && NS == 1>(sm, nfft, base_of, src_of,
-                                                               stw + smem_twiddle_offset(N, NS));
-        fft_passes_ct<R, N, E, NS * RAD, INV, GIN>(sm, nfft, base_of, src_of, stw);
+                                                               stw + smem_twiddle_offset(N, NS), hook);
+        fft_passes_ct<R, N, E, NS * RAD, INV, GIN>(sm, nfft, base_of, src_of, stw, hook);
     }
 }
 
 // nfft transforms of length N held in shared memory (GIN: read from global memory).
-template <typename R, int N, bool INV, bool GIN = false, typename BaseFn, typename SrcFn = NoSrc>
+template <typename R, int N, bool INV, bool GIN = false, typename BaseFn, typename SrcFn = NoSrc,
+          typename Hook = NoHook>
 __device__ __forceinline__ void fft_many_ct(cpx<R>* sm, int nfft, BaseFn base_of, const cpx<R>* stw,
-                                            SrcFn src_of = SrcFn())
+                                            SrcFn src_of = SrcFn(), Hook hook = Hook())
 {
-    fft_passes_ct<R, N, elems_per_thread(N), 1, INV, GIN>(sm, nfft, base_of, src_of, stw);
+    fft_passes_ct<R, N, elems_per_thread(N), 1, INV, GIN>(sm, nfft, base_of, src_of, stw, hook);
 }
 
 // e^{-2 pi i num / den}

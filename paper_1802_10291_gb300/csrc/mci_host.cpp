@@ -714,10 +714,11 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         cd_.Q = hc.s * p->n_out;
         cd_.QM = std::max(cd_.M_in, cd_.Q);
         cd_.npad = padded_len(hc.N);
+        cd_.sstride = cd_.QM * cd_.npad + (((2 - cd_.QM * cd_.npad) % 16) + 16) % 16;
         cd_.mag_min = fastdiv_magic(cd_.M_in);
         cd_.mag_q = fastdiv_magic(cd_.Q);
         cd_.mag_nout = fastdiv_magic(cd_.n_out);
-        const int per = cd_.QM * cd_.npad * csz + smem_twiddle_count(hc.N) * csz;
+        const int per = cd_.sstride * csz + smem_twiddle_count(hc.N) * csz;
         if (per > smem_cap) {
             delete p;
             return MCI_ERR_UNSUPPORTED_SIZE;
@@ -728,7 +729,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     p->csmem.resize(n);
     for (int c = 0; c < n; ++c) {
         ClassDev& cd_ = p->cdev[c];
-        const int per = cd_.QM * cd_.npad * csz;
+        const int per = cd_.sstride * csz;
         const int twb = smem_twiddle_count(cd_.N) * csz;   // FFT twiddles after the buffers
         cd_.G = std::max(1, std::min(kMaxTile, (budget - twb) / per));
         p->csmem[c] = cd_.G * per + twb;

@@ -72,6 +72,9 @@ struct ClassDev {
     int G;       // signals per tile
     int n_out;   // outputs per signal
     int npad;    // padded FFT buffer length (complex elements)
+    int sstride; // shared-memory stride between the tile's signals (complex elements):
+                 // QM * npad rounded up to 2 mod 16, so that the buffers of consecutive
+                 // signals start on different banks (16-byte aligned)
     int64_t w_off;   // offset of this class's bin weights W[k][m][q], k = 0..N
     uint64_t mag_min, mag_q, mag_nout;   // fastdiv_magic of M_in, Q and n_out
 };

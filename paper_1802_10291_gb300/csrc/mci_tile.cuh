@@ -127,7 +127,7 @@ __device__ __forceinline__ void combine_loop(cpx<R>* sm, const ClassDev& c, int 
 {
     const int total = (c.N / 2 + 1) * gcount;
     const R two_over_p = R(2) / R(c.P);
-    const int QMn = c.QM * c.npad;
+    const int sst = c.sstride;
     // item it = k * gcount + g; (k, g) advance incrementally (no division in the loop)
     const int it0 = ltid();
     const int step = blockDim.x;
@@ -135,7 +135,7 @@ __device__ __forceinline__ void combine_loop(cpx<R>* sm, const ClassDev& c, int 
     int k = it0 / gcount, g = it0 - k * gcount;
     for (int it = it0; it < total; it += step) {
         const cpx<R> w = cis_neg_pi<R>(R(k) * two_over_p);  // e^{-2 pi i k / P}
-        combine_pair<R, MIN, QC>(sm + g * QMn, c, k, W, w);
+        combine_pair<R, MIN, QC>(sm + g * sst, c, k, W, w);
         k += dk;
         g += dg;
         if (g >= gcount) {
@@ -161,12 +161,12 @@ __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int 
 
 // Buffer f of a tile with `cnt` transforms per signal: signal f / cnt, slot f % cnt.
 struct SlotBase {
-    int cnt, QM, npad;
+    int cnt, sstride, npad;
     uint64_t mag;   // fastdiv_magic(cnt)
     __device__ __forceinline__ int operator()(int f) const
     {
         const int g = fastdiv(f, mag);
-        return (g * QM + (f - g * cnt)) * npad;
+        return g * sstride + (f - g * cnt) * npad;
     }
 };
 
@@ -188,22 +188,25 @@ struct SrcContig {
 // gin != nullptr: the tile's signals are read by the first forward pass directly
 // from gin + s_in[g] (8-byte aligned); otherwise they are already in shared memory.
 // The FFT twiddles live after the tile's buffers (smem_twiddle_offset); they are
-// filled here, before the first pass, which needs none and ends with a barrier.
+// filled here, before or during the first pass, which needs none and ends with a barrier.
 template <typename R, int N>
 __device__ __forceinline__ void compute_tile(cpx<R>* sm, const ClassDev& c, int gcount,
                                              const cpx<R>* __restrict__ W, const R* gin = nullptr,
                                              const int64_t* s_in = nullptr)
 {
-    cpx<R>* stw = sm + c.G * c.QM * c.npad;
-    fill_twiddles_ct<R, N, elems_per_thread(N), 1>(stw);
-    if (gin)
-        fft_many_ct<R, N, false, true>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad, c.mag_min}, stw,
-                                       SrcContig<R>{gin, s_in, c.M_in, c.P, c.mag_min});
-    else
-        fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.QM, c.npad, c.mag_min}, stw);
+    cpx<R>* stw = sm + c.G * c.sstride;
+    auto fill = [stw] { fill_twiddles_ct<R, N, elems_per_thread(N), 1>(stw); };
+    if (gin) {
+        // the twiddles are computed while the first pass's global loads are in flight
+        fft_many_ct<R, N, false, true>(sm, gcount * c.M_in, SlotBase{c.M_in, c.sstride, c.npad, c.mag_min}, stw,
+                                       SrcContig<R>{gin, s_in, c.M_in, c.P, c.mag_min}, fill);
+    } else {
+        fill();
+        fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.sstride, c.npad, c.mag_min}, stw);
+    }
     combine_tile<R>(sm, c, gcount, W);
     __syncthreads();
-    fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.QM, c.npad, c.mag_q}, stw);
+    fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.sstride, c.npad, c.mag_q}, stw);
 }
 
 // ---------------------------------------------------------------------------
@@ -228,7 +231,7 @@ template <typename R>
 __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const R* __restrict__ in,
                                             const int64_t* off, int gcount)
 {
-    const int P = c.P, Min = c.M_in, npad = c.npad, QM = c.QM;
+    const int P = c.P, Min = c.M_in, npad = c.npad, sst = c.sstride;
     const int per = Min * P;
     constexpr int VW = sizeof(R) == 4 ? 4 : 2;  // reals per 16-byte copy
     bool vec = (P % VW) == 0;
@@ -239,14 +242,14 @@ __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const
             const int g = t / nv, v = t - g * nv;
             const int i = v * VW;
             const int m = i / P, p = (i - m * P) >> 1;
-            cp_async16(&sm[(g * QM + m) * npad + pad16(p)], in + off[g] + i);
+            cp_async16(&sm[g * sst + m * npad + pad16(p)], in + off[g] + i);
         }
         cp_async_wait_all();
     } else {
         for (int t = ltid(); t < gcount * per; t += blockDim.x) {
             const int g = t / per, i = t - g * per;
             const int m = i / P, pp = i - m * P;
-            R* d = reinterpret_cast<R*>(&sm[(g * QM + m) * npad + pad16(pp >> 1)]);
+            R* d = reinterpret_cast<R*>(&sm[g * sst + m * npad + pad16(pp >> 1)]);
             d[pp & 1] = in[off[g] + i];
         }
     }
@@ -263,7 +266,7 @@ template <typename R, int N>
 __device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
                                              const int64_t* off, int gcount)
 {
-    const int T = c.T, s = c.s, npad = c.npad, QM = c.QM, nout = c.n_out;
+    const int T = c.T, s = c.s, npad = c.npad, sst = c.sstride, nout = c.n_out;
     constexpr int VR = 16 / sizeof(R);     // reals per 16-byte vector
     bool vec = (s % VR) == 0 && (T % VR) == 0, vec2 = sizeof(R) == 4 && (s % 2) == 0;
     for (int g = 0; g < gcount; ++g) {
@@ -275,7 +278,7 @@ __device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c
         const int go = t / N;                    // compile-time N: shift or multiply
         const int l = t - go * N;
         const int g = fastdiv(go, c.mag_nout), o = go - g * nout;
-        const cpx<R>* src = sm + (g * QM + o * s) * npad + pad16(l);
+        const cpx<R>* src = sm + g * sst + o * s * npad + pad16(l);
         R* dst = out + off[g] + (int64_t)o * T + (int64_t)2 * l * s;
         if (vec) {
             for (int u = 0; u < s; u += VR) {
@@ -312,11 +315,11 @@ template <typename R>
 __device__ __forceinline__ void load_cols(cpx<R>* sm, const ClassDev& c, const R* __restrict__ in,
                                           int64_t base, int64_t ld, int gcount)
 {
-    const int P = c.P, npad = c.npad, QM = c.QM;
+    const int P = c.P, sst = c.sstride;
     const int total = P * gcount;
     for (int i = ltid(); i < total; i += blockDim.x) {
         const int p = i / gcount, g = i - p * gcount;
-        R* d = reinterpret_cast<R*>(&sm[g * QM * npad + pad16(p >> 1)]);
+        R* d = reinterpret_cast<R*>(&sm[g * sst + pad16(p >> 1)]);
         d[p & 1] = __ldg(in + base + g + (int64_t)p * ld);
     }
 }
@@ -325,12 +328,12 @@ template <typename R>
 __device__ __forceinline__ void store_cols(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
                                            int64_t base, int64_t ld, int gcount)
 {
-    const int T = c.T, s = c.s, npad = c.npad, QM = c.QM;
+    const int T = c.T, s = c.s, npad = c.npad, sst = c.sstride;
     const int total = T * gcount;
     for (int i = ltid(); i < total; i += blockDim.x) {
         const int x = i / gcount, g = i - x * gcount;
         const int l2 = x / s, u = x - l2 * s;
-        const cpx<R> z = sm[(g * QM + u) * npad + pad16(l2 >> 1)];
+        const cpx<R> z = sm[g * sst + u * npad + pad16(l2 >> 1)];
         out[base + g + (int64_t)x * ld] = (l2 & 1) ? z.y : z.x;
     }
 }
