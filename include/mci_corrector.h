@@ -7,7 +7,9 @@
  * This is that: a 5-layer 3x3 convolutional network f with channels
  * 1 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU between layers, bias, periodic padding,
  * applied to an MCI reconstruction x:  pred = x + f(x).  Weights are BF16 in
- * the convolutions (FP32 master copies), activations and accumulation FP32.
+ * the convolutions (FP32 master copies), activations and accumulation FP32; the
+ * 32 -> 32 convolutions run on the tensor cores with each FP32 activation split
+ * into two BF16 terms (hi + lo), the others on the CUDA cores.
  * Training minimises the mean squared error of pred against the HR image with
  * Adam (beta1 0.9, beta2 0.999, eps 1e-8).  Plain MCI stays the fallback: with
  * the last layer's weights and bias zero, pred = x exactly.
@@ -60,6 +62,11 @@ mci_status mci_corrector_train_step(mci_corrector_t net, const float* mci, const
  * moments) and the Adam step count.  Both synchronise the device. */
 mci_status mci_corrector_get_state(mci_corrector_t net, float* host, int* step);
 mci_status mci_corrector_set_state(mci_corrector_t net, const float* host, int step);
+
+/* Device-side error word of the corrector's kernels since the last call: bit 0 = a
+ * tensor-core completion wait gave up (the tile was skipped; outputs are invalid).
+ * Synchronises the device and clears the word. */
+mci_status mci_corrector_status(mci_corrector_t net, int* status);
 
 mci_status mci_corrector_destroy(mci_corrector_t net);
 

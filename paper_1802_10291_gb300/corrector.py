@@ -29,11 +29,12 @@ def _lib():
         lib.mci_corrector_get_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
         lib.mci_corrector_set_state.argtypes = [vp, vp, ctypes.c_int]
         lib.mci_corrector_destroy.argtypes = [vp]
+        lib.mci_corrector_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         lib.mci_generate_images.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
         lib.mci_decimate.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
         for f in ("mci_corrector_create", "mci_corrector_forward", "mci_corrector_loss_grad",
                   "mci_corrector_train_step", "mci_corrector_get_state", "mci_corrector_set_state",
-                  "mci_corrector_destroy", "mci_generate_images", "mci_decimate"):
+                  "mci_corrector_destroy", "mci_corrector_status", "mci_generate_images", "mci_decimate"):
             getattr(lib, f).restype = ctypes.c_int
         _bound = True
     return lib
@@ -106,6 +107,12 @@ class Corrector:
         mci._check(_lib().mci_corrector_get_state(self.handle, buf.ctypes.data, ctypes.byref(step)),
                    "mci_corrector_get_state")
         return buf, step.value
+
+    def status(self) -> int:
+        """Device error word since the last call (0 = no error); synchronises."""
+        st = ctypes.c_int()
+        mci._check(_lib().mci_corrector_status(self.handle, ctypes.byref(st)), "mci_corrector_status")
+        return st.value
 
     def set_state(self, buf, step):
         buf = np.ascontiguousarray(buf, np.float32)

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "mci_corrector.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -173,6 +174,195 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_wgrad_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// 32 -> 32 channel 3x3 conv on the tensor cores (tcgen05), used for the hidden
+// layers' forward convs and their data-gradient convs.
+//
+// Implicit GEMM per tile of 4 image rows x 32 pixels (M = 128 pixels, N = 32
+// output channels): out[p][co] = sum over taps t and input channels ci of
+// A_t[p][ci] B_t[co][ci], A_t[p] = x(p + d_t).  The FP32 input is split as
+// x = hi + lo, two BF16 values, and one pixel row of A holds [hi(ci 0..31) |
+// lo(ci 0..31)] (64 BF16 = one 128-byte swizzle row); B_t rows hold the BF16
+// weights twice, [w(ci 0..31) | w(ci 0..31)], so one K = 64 contraction gives
+// hi*w + lo*w with FP32 accumulation (the weights are exact in BF16, the
+// split leaves an input error near 2^-17 relative).  Shared memory holds three
+// copies of the tile's 6 x 32 halo rows shifted by dx = -1, 0, +1; the A
+// operand of tap (dy, dx) is rows (dy + 1) * 32 .. + 127 of copy dx, which
+// starts on a 1024-byte swizzle-atom boundary, so every tap is a plain
+// descriptor offset.  Nine taps x four K = 16 MMAs per tile, issued by one
+// thread; the accumulator (128 lanes x 32 FP32 columns of tensor memory) is
+// read back with tcgen05.ld, one pixel per thread.  Persistent CTAs, two per SM.
+// ---------------------------------------------------------------------------
+constexpr int kTcThreads = 128;
+constexpr int kTcRows = 4, kTcCols = 32;                       // 4 x 32 = 128 MMA rows
+constexpr int kTcHaloRows = kTcRows + 2;
+constexpr int kTcHaloCols = kTcCols + 2;
+constexpr int kTcCopyBytes = kTcHaloRows * kTcCols * 128;      // one dx-shifted copy
+constexpr int kTcTapBytes = kWide * 128;                       // one tap's weights
+constexpr int kTcSmem = 3 * kTcCopyBytes + 9 * kTcTapBytes + 1024;
+
+__device__ __forceinline__ int wrapg(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ uint32_t bf16_pair_bits(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__global__ void __launch_bounds__(kTcThreads) conv32_tc_kernel(
+    const float* __restrict__ x, const __nv_bfloat16* __restrict__ w, bool transposed_w,
+    const float* __restrict__ bias, const float* __restrict__ mask, float* __restrict__ out, int B, int H,
+    int W, bool relu, int* status)
+{
+    using namespace mci;
+    extern __shared__ __align__(1024) unsigned char tsm_raw[];
+    char* sbase = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~uintptr_t(1023));
+    char* Acp = sbase;                        // copies dx = -1, 0, +1
+    char* Bw = sbase + 3 * kTcCopyBytes;      // taps 0..8
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // B_t[co][.] = [w(co, ci = 0..31, t) | the same], BF16 bits copied as they are
+    for (int i = tid; i < 9 * kWide * 4; i += kTcThreads) {
+        const int t = i / (kWide * 4), co = (i >> 2) % kWide, j = i & 3;
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c0 = j * 8 + 2 * e;
+            __nv_bfloat16 v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ci = c0 + h;
+                v[h] = transposed_w ? w[((int64_t)ci * kWide + co) * 9 + (8 - t)]
+                                    : w[((int64_t)co * kWide + ci) * 9 + t];
+            }
+            pk[e] = bf16_pair_bits(v[0], v[1]);
+        }
+        const uint4 q = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        char* tap = Bw + t * kTcTapBytes;
+        *reinterpret_cast<uint4*>(tap + sw128_offset(co, j * 8)) = q;
+        *reinterpret_cast<uint4*>(tap + sw128_offset(co, kWide + j * 8)) = q;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(32) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_bf16_f32(128, kWide);
+
+    const int64_t plane = (int64_t)H * W;
+    const int tiles_x = (W + kTcCols - 1) / kTcCols, tiles_y = (H + kTcRows - 1) / kTcRows;
+    const int n_tiles = B * tiles_y * tiles_x;
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int b = tile / (tiles_y * tiles_x);
+        const int r2 = tile - b * tiles_y * tiles_x;
+        const int y0 = (r2 / tiles_x) * kTcRows, x0 = (r2 % tiles_x) * kTcCols;
+        const float* xb = x + (int64_t)b * kWide * plane;
+        const float* mb = mask ? mask + (int64_t)b * kWide * plane : nullptr;
+        // halo pixel (r, h) = image pixel (y0 - 1 + r, x0 - 1 + h), periodic; it is row
+        // r * 32 + (h - 1 - dx) of copy dx where that index lies in 0..31
+        for (int it = tid; it < kTcHaloRows * kTcHaloCols; it += kTcThreads) {
+            const int r = it / kTcHaloCols, h = it - r * kTcHaloCols;
+            const int64_t pix = (int64_t)wrapg(y0 - 1 + r, H) * W + wrapg(x0 - 1 + h, W);
+            float v[kWide];
+#pragma unroll
+            for (int c = 0; c < kWide; ++c) v[c] = xb[c * plane + pix];
+            if (mb) {
+#pragma unroll
+                for (int c = 0; c < kWide; ++c)
+                    if (!(mb[c * plane + pix] > 0.f)) v[c] = 0.f;
+            }
+            uint4 hi[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t ph[4], pl[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c0 = j * 8 + 2 * e;
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[c0]), h1 = __float2bfloat16_rn(v[c0 + 1]);
+                    ph[e] = bf16_pair_bits(h0, h1);
+                    pl[e] = bf16_pair_bits(__float2bfloat16_rn(v[c0] - __bfloat162float(h0)),
+                                           __float2bfloat16_rn(v[c0 + 1] - __bfloat162float(h1)));
+                }
+                hi[j] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                lo[j] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+            }
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int px = h - 1 - dx;
+                if (px >= 0 && px < kTcCols) {
+                    char* cp = Acp + (dx + 1) * kTcCopyBytes;
+                    const int row = r * kTcCols + px;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        *reinterpret_cast<uint4*>(cp + sw128_offset(row, j * 8)) = hi[j];
+                        *reinterpret_cast<uint4*>(cp + sw128_offset(row, kWide + j * 8)) = lo[j];
+                    }
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int dy = t / 3 - 1, dx = t % 3 - 1;
+                const uint32_t a0 = smem_u32(Acp + (dx + 1) * kTcCopyBytes + (dy + 1) * kTcCols * 128);
+                const uint32_t b0 = smem_u32(Bw + t * kTcTapBytes);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)   // K = 16 per MMA: 32 bytes into the 128-byte row
+                    mma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
+                             t > 0 || kk > 0);
+            }
+            mma_commit(smem_u32(&bar));
+        }
+        if (!mbar_wait(smem_u32(&bar), phase)) {
+            atomicOr(status, 1);
+            s_abort = 1;
+        }
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+            const int y = y0 + tid / kTcCols, xq = x0 + tid % kTcCols;
+            if (!s_abort && y < H && xq < W) {
+                float* ob = out + (int64_t)b * kWide * plane + (int64_t)y * W + xq;
+#pragma unroll
+                for (int co = 0; co < kWide; ++co) {
+                    float val = __uint_as_float(v[co]) + (bias ? bias[co] : 0.f);
+                    if (relu) val = fmaxf(val, 0.f);
+                    ob[co * plane] = val;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (s_abort) break;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
+    }
+}
+
 // d pred: grad = 2 (pred - hr) / n, loss += sum (pred - hr)^2 / n
 __global__ void mse_kernel(const float* __restrict__ pred, const float* __restrict__ hr, float* __restrict__ grad,
                            float* __restrict__ loss, int64_t n)
@@ -273,6 +463,7 @@ struct mci_corrector_s {
     float* act = nullptr;           // layer outputs: kLayers - 1 hidden [B][32][H][W] + pred
     float* gbuf[2] = {nullptr, nullptr};
     float* loss = nullptr;
+    int* status = nullptr;          // device: bit 0 = a tensor-core wait timed out
     int step = 0;
 };
 
@@ -290,10 +481,29 @@ int corrector_param_layout(int* woff, int* boff)
     return n;
 }
 
+int tc_grid_limit()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        n = 2 * (sms > 0 ? sms : 1);
+        cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    }
+    return n;
+}
+
 cudaError_t conv(const float* x, int cin, int cout, const __nv_bfloat16* w, bool tw, const float* bias,
                  const float* mask, const float* res, float* out, int B, int H, int W, bool relu,
-                 cudaStream_t s)
+                 cudaStream_t s, int* status)
 {
+    if (cin == kWide && cout == kWide && !res) {
+        const int tiles = B * ((H + kTcRows - 1) / kTcRows) * ((W + kTcCols - 1) / kTcCols);
+        const int grid = tiles < tc_grid_limit() ? tiles : tc_grid_limit();
+        conv32_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(x, w, tw, bias, mask, out, B, H, W, relu, status);
+        return cudaGetLastError();
+    }
     const dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, B);
     const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cin * 9 * cout);
     if (cout == kWide) {
@@ -335,7 +545,7 @@ cudaError_t forward(mci_corrector_t c, const float* mci, float* pred, int B, int
         const bool last = l == kLayers - 1;
         float* y = last ? pred : hidden(c, l, pix);
         e = conv(x, cin_of(l), cout_of(l), c->wbf + c->woff[l], false, c->master + c->boff[l], nullptr,
-                 last ? mci : nullptr, y, B, H, W, !last, s);
+                 last ? mci : nullptr, y, B, H, W, !last, s, c->status);
         x = y;
     }
     return e;
@@ -357,7 +567,7 @@ cudaError_t backward(mci_corrector_t c, const float* mci, const float* gpred, in
             // gradient w.r.t. layer l's input = hidden(l - 1): conv with transposed, reversed weights
             float* gin = c->gbuf[gi];
             e = conv(g, cout_of(l), cin_of(l), c->wbf + c->woff[l], true, nullptr, gmask, nullptr, gin, B, H,
-                     W, false, s);
+                     W, false, s, c->status);
             g = gin;
             gi ^= 1;
         }
@@ -391,6 +601,8 @@ mci_status mci_corrector_create(mci_corrector_t* out, int64_t max_pixels, const 
     if (e == cudaSuccess) e = cudaMalloc(&c->gbuf[0], sizeof(float) * max_pixels * kWide * 2);
     if (e == cudaSuccess) c->gbuf[1] = c->gbuf[0] + max_pixels * kWide;
     if (e == cudaSuccess) e = cudaMalloc(&c->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->master, 0, sizeof(float) * n * 4, s);
     if (e == cudaSuccess && init_params)
         e = cudaMemcpyAsync(c->master, init_params, sizeof(float) * n, cudaMemcpyHostToDevice, s);
@@ -422,6 +634,7 @@ mci_status mci_corrector_destroy(mci_corrector_t c)
     cudaFree(c->act);
     cudaFree(c->gbuf[0]);
     cudaFree(c->loss);
+    cudaFree(c->status);
     delete c;
     return MCI_OK;
 }
@@ -494,6 +707,15 @@ mci_status mci_corrector_set_state(mci_corrector_t c, const float* host, int ste
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     c->step = step;
+    return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_corrector_status(mci_corrector_t c, int* status)
+{
+    if (!c || !status) return MCI_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(status, c->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
     return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
 }
 

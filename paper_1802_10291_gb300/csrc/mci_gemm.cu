@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "mci_internal.h"
+#include "tc_ptx.cuh"
 
 namespace mci {
 
@@ -27,90 +28,6 @@ constexpr int kTileN = 128;
 constexpr int kChunkK = 64;                               // one 128-byte swizzle atom of BF16
 constexpr int kPlane = kTileM * kChunkK * 2;              // bytes of one 128 x 64 BF16 plane
 constexpr int kGemmSmem = 6 * kPlane + 1024;              // 3 A planes + 3 B planes + alignment
-constexpr long long kWaitLimit = 1ll << 26;               // bounded mbarrier wait (iterations)
-
-// ---------------------------------------------------------------------------
-// PTX helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-// Wait for the mbarrier phase `parity`; false after kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    for (long long it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups
-// 1024 bytes apart.  Fields: start address >> 4 (bits 0-13), leading byte offset >> 4
-// (16-29, unused for this layout: 1), stride byte offset >> 4 (32-45), descriptor
-// version 1 (46-47), layout type 2 = 128-byte swizzle (61-63).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3fff);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
-// M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         bool accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 ::"r"(bar) : "memory");
-}
-
-// 128-byte-swizzled K-major address of 8-byte group (row r, BF16 column k, k % 4 == 0)
-// inside one 128 x 64 plane: 16-byte chunk k/8 of row r lives at chunk (k/8) ^ (r % 8).
-__device__ __forceinline__ uint32_t sw128_offset(int r, int k)
-{
-    return (uint32_t)(r * 128 + ((((k >> 3) ^ (r & 7)) << 4)) + ((k & 7) << 1));
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
-{
-    const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
-    return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
-}
 
 // Split four FP32 values into three BF16 planes (h, m, l) and store them.
 __device__ __forceinline__ void split_store(const float4 v, char* plane_h, uint32_t off)

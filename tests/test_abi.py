@@ -15,7 +15,7 @@ def test_exports_every_declared_symbol(mci_lib):
                              "mci_destroy", "mci_error_string", "mci_interp_1d_noalloc",
                              "mci_corrector_num_params", "mci_corrector_create", "mci_corrector_forward",
                              "mci_corrector_loss_grad", "mci_corrector_train_step",
-                             "mci_corrector_get_state", "mci_corrector_set_state",
+                             "mci_corrector_get_state", "mci_corrector_set_state", "mci_corrector_status",
                              "mci_corrector_destroy", "mci_generate_images", "mci_decimate"}
     for name in declared:
         assert hasattr(mci_lib, name), name

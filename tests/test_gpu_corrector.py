@@ -38,7 +38,7 @@ def _oracle_params(p32):
     return p
 
 
-@pytest.mark.parametrize("shape", [(2, 20, 24), (1, 33, 17), (3, 16, 16)])
+@pytest.mark.parametrize("shape", [(2, 20, 24), (1, 33, 17), (3, 16, 16), (1, 37, 70)])
 def test_forward_and_gradient_parity(cuda_device, shape):
     import torch
     from paper_1802_10291_gb300 import corrector
@@ -56,6 +56,7 @@ def test_forward_and_gradient_parity(cuda_device, shape):
     L = torch.empty(1, device="cuda")
     net.loss_grad(xd, hd, b, h, w, grad=g, loss=L)
     torch.cuda.synchronize()
+    assert net.status() == 0
     po = _oracle_params(p32)
     pred, _ = oc.forward(po, x.astype(np.float64))
     Lo, go = oc.loss_grad(po, x.astype(np.float64), hr.astype(np.float64))
