@@ -36,6 +36,17 @@ WORKLOAD = ("batched 1-D MCI: 16384 signals, M=3 {identity, Hilbert -i sgn, deri
             "P ~ U{256,512,1024,2048,4096}, T=4P, half trig polynomials, half exp(a cos(t-phi))")
 
 
+# Signals per size class in the CPU-oracle sample (about 10 s on 16 host cores); the
+# same sample gives the realised FP32/FP64 errors.
+CPU_PER_CLASS = 100
+
+# DRAM bytes (read + write) per signal of the timed roofline kernel (mci_kernel<float, 2048>,
+# P = 4096, M = 3, T = 16384), from one ncu capture of that launch (3201 signals:
+# 157.65 MB read + 150.64 MB written; profiles/mci_kernel_f32_n2048_p4096.md).
+# None whenever the kernel has changed since the capture.
+ROOFLINE_TRAFFIC_PER_SIGNAL = (157649920 + 150635776) / 3201
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -45,10 +56,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def make_batch(rank: int):
+def make_batch(rank: int, n_signals: int = N_SIGNALS):
+    """This rank's own batch: seeded by the rank, so ranks process different signals."""
     from paper_1802_10291_gb300 import synth
     rng = synth.rng_for(1, 1000 + rank)
-    b = synth.uneven_batch_1d(rng, N_SIGNALS, P_CHOICES, SYSTEMS)
+    b = synth.uneven_batch_1d(rng, n_signals, P_CHOICES, SYSTEMS)
     P_of = b["P"]
     cls = np.searchsorted(np.asarray(P_CHOICES), P_of).astype(np.int32)
     flat = np.concatenate([g.ravel() for g in b["g"]])
@@ -110,24 +122,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(n_gpus: int):
+def dist_setup(n_gpus: int, backend: str = "nccl"):
+    """(world, rank, local rank) from the torchrun environment; joins the process group
+    when world > 1 (NCCL on the GPU machine; the CPU tests use gloo)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return world, rank, local
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """Maximum of x over all ranks (the step time every rank reports is the slowest one)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, max_seconds: float) -> float:
+    """Weak scaling: every rank processes its own batch of units_per_rank per step, so the
+    job's throughput is all ranks' units over the slowest rank's time (units/s)."""
+    return units_per_rank * world * steps / max_seconds
 
 
 def barrier(world: int):
@@ -436,7 +459,7 @@ def main():
     secs, clocks = timed(lambda: step(plan32, x32, y32, sc), args.steps, args.warmup)
     secs = max_over_ranks(secs, world)
     out_samples = batch["n_out"] * world
-    value = out_samples * args.steps / secs / 1e6
+    value = whole_job_rate(batch["n_out"], world, args.steps, secs) / 1e6
     st = plan32.info()
     assert st["device_status"] == 0, st
     if args.quick:
@@ -493,7 +516,7 @@ def main():
     cpu = None
     err = None
     if rank == 0 and not args.no_cpu_baseline:
-        idx = oracle_sample(batch, n_per_class=12)
+        idx = oracle_sample(batch, n_per_class=CPU_PER_CLASS)
         ref, cpu_s = run_oracle(batch, idx)
         yh = y32.cpu().double().numpy()
         yh64 = y64.cpu().numpy()
@@ -513,8 +536,8 @@ def main():
         n_cpu_out = sum(S_FACTOR * int(batch["P"][b]) for b in idx)
         cpu = {"value": n_cpu_out / cpu_s / 1e6, "unit": UNIT, "cores": os.cpu_count(),
                "kind": "oracle",
-               "sample": f"{len(idx)} signals, 12 of each P class (6 trig, 6 smooth), FP64 direct "
-                         f"sum formula, {cpu_s:.1f} s"}
+               "sample": f"{len(idx)} signals, {CPU_PER_CLASS} of each P class (half trig, half smooth), "
+                         f"FP64 direct sum formula, {cpu_s:.1f} s"}
 
     if rank == 0:
         line = {
@@ -530,7 +553,9 @@ def main():
             "clocks": clocks,
             "gpu_launches": n_cls * args.steps,
             "roofline": {"bound": "hbm", "achieved": k_achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": k_achieved / hbm, "traffic": None,
+                         "frac": k_achieved / hbm,
+                         "traffic": (None if ROOFLINE_TRAFFIC_PER_SIGNAL is None
+                                     else ROOFLINE_TRAFFIC_PER_SIGNAL * sel.size),
                          "kernel": "mci_kernel<float, N=2048> (P=4096 tiles), timed alone",
                          "bytes_per_launch": k_bytes, "ms_per_launch": k_ms,
                          "peak_source": f"{peak_kind} hbm_gbs"},
