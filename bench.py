@@ -378,7 +378,7 @@ def main():
 
     def setup(prec):
         dt = torch.float32 if prec == "fp32" else torch.float64
-        plan = mci.Plan(SYSTEMS, P_CHOICES, T, precision=prec, max_batch=N_SIGNALS)
+        plan = mci.Plan(SYSTEMS, P_CHOICES, T, precision=prec, max_batch=N_SIGNALS, autotune=True)
         x = torch.tensor(batch["flat"], dtype=dt, device=dev)
         y = torch.empty(batch["n_out"], dtype=dt, device=dev)
         sc = np.ascontiguousarray(batch["cls"], dtype=np.int32)   # host: host-grouped launches
@@ -472,6 +472,14 @@ def main():
     d_sc = torch.tensor(sc, device=dev)
     secs_dev, _ = timed(lambda: step(plan32, x32, y32, d_sc), max(20, args.steps // 4), 3)
     ms_dev = 1e3 * secs_dev / max(20, args.steps // 4)
+    # ... and that device-grouped step captured once in a CUDA graph and replayed
+    mci.mci_interp_1d_noalloc(plan32.handle, x32, None, y32, None, d_sc, N_SIGNALS, stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        mci.mci_interp_1d_noalloc(plan32.handle, x32, None, y32, None, d_sc, N_SIGNALS)
+    secs_graph, _ = timed(graph.replay, max(20, args.steps // 4), 3)
+    ms_graph = 1e3 * secs_graph / max(20, args.steps // 4)
 
     # roofline of the step's interpolation kernels: algorithmic bytes = samples in + out
     hbm, peak_kind = peaks()
@@ -563,7 +571,8 @@ def main():
                               "bytes_per_step": bytes_step},
             "device_grouped": {"ms_per_step": ms_dev, "value": out_samples / (ms_dev / 1e3) / 1e6,
                                "unit": UNIT, "note": "size classes in device memory: grouping "
-                               "and per-class launches on the device"},
+                               "and per-class launches on the device",
+                               "cuda_graph_ms_per_step": ms_graph},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * secs64 / steps64,
                      "speedup_fp32_over_fp64": value / value64},
             "err_vs_oracle": err,

@@ -122,6 +122,12 @@ typedef struct {
     int64_t max_images;      /* most images one mci_upsample_2d call passes (0: no 2-D)    */
     int64_t max_intermediate;/* most row-pass pixels one mci_upsample_2d call needs:
                                 sum over images of h * s * w (0: no 2-D)                   */
+    int autotune;            /* 0: tile height G (signals per CTA) from a fixed shared-memory
+                                budget; 1: mci_plan times candidate G for every size class
+                                on a scratch batch (zeros, about 64 MB of device memory held
+                                during the call) and keeps the fastest.  Results do not
+                                depend on G; plan creation takes longer (milliseconds per
+                                class).  There is no counterpart in the paper.           */
 } mci_desc;
 
 typedef struct {

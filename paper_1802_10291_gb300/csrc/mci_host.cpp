@@ -664,6 +664,84 @@ mci_status mci_destroy(mci_plan_t p)
     return MCI_OK;
 }
 
+// Plan-time tile autotuner: for every size class, time the uniform 1-D launch of a
+// scratch batch for each candidate tile height G (signals per CTA; the candidates come
+// from shared-memory budgets of 16 .. 144 KB per CTA, i.e. 1 .. 12 CTAs per SM) and keep
+// the fastest.  The results of a launch do not depend on G.
+static cudaError_t autotune_tiles(mci_plan_s* p, int smem_cap, cudaStream_t s)
+{
+    const int n = (int)p->cls.size();
+    const int csz = (int)(2 * p->elem);
+    const size_t scratch_bytes = (size_t)64 << 20;
+    void* scratch = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, scratch_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(scratch, 0, scratch_bytes, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int c = 0; c < n && e == cudaSuccess; ++c) {
+        ClassDev cd = p->cdev[c];
+        const int per = cd.sstride * csz;
+        const int twb = smem_twiddle_count(cd.N) * csz;
+        const int64_t sig_bytes = (int64_t)(cd.M_in * cd.P + cd.n_out * cd.T) * p->elem;
+        const int64_t nsig = std::max<int64_t>(1, std::min<int64_t>((int64_t)scratch_bytes / sig_bytes, 8192));
+        std::vector<int> cand;
+        for (int budget : {16 << 10, 24 << 10, 32 << 10, 48 << 10, 64 << 10, 96 << 10, 144 << 10}) {
+            const int G = std::max(1, std::min(kMaxTile, (budget - twb) / per));
+            if (G * per + twb <= smem_cap && std::find(cand.begin(), cand.end(), G) == cand.end())
+                cand.push_back(G);
+        }
+        int bestG = cd.G;
+        float best = 1e30f;
+        for (int G : cand) {
+            cd.G = G;
+            KArgs a{};
+            a.c = cd;
+            a.cls = c;
+            a.mode = kModeUniform;
+            a.W = p->launch[c].W;
+            a.in = scratch;
+            a.out = (char*)scratch + nsig * (int64_t)cd.M_in * cd.P * p->elem;
+            a.batch = nsig;
+            a.status = p->d_status;
+            const int64_t items = (nsig + G - 1) / G;
+            a.uniform_items = (int)items;
+            void* args[] = {&a};
+            const size_t smem = (size_t)G * per + twb;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)   // warm-up
+                e = cudaLaunchKernel(p->kern[c], dim3((unsigned)items), dim3(kThreads), args, smem, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep)
+                e = cudaLaunchKernel(p->kern[c], dim3((unsigned)items), dim3(kThreads), args, smem, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                bestG = G;
+            }
+        }
+        p->cdev[c].G = bestG;
+        p->csmem[c] = bestG * per + twb;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaError_t ef = cudaFree(scratch);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess) {
+        p->smem = 0;
+        for (int c = 0; c < n; ++c) {
+            p->smem = std::max(p->smem, p->csmem[c]);
+            p->launch[c].c = p->cdev[c];
+            p->launch[c].smem = p->csmem[c];
+        }
+        e = cudaMemcpyAsync(p->d_launch, p->launch.data(), sizeof(ClassLaunch) * n, cudaMemcpyHostToDevice, s);
+    }
+    return e;
+}
+
 mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
 {
     if (!out) return MCI_ERR_INVALID_ARG;
@@ -907,6 +985,8 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_stage2[i], cudaEventDisableTiming);
         }
     }
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int) * 4, s);
+    if (e == cudaSuccess && d.autotune) e = autotune_tiles(p, smem_cap, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int) * 4, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

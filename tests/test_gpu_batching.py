@@ -1,0 +1,97 @@
+"""Batching machinery of the 1-D path: the plan-time tile autotuner (results must not
+depend on the tile height it picks) and CUDA-graph capture of the launches that allow
+it (uniform batches; device-side grouping through the no-allocation entry point)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1802_10291_gb300 import mci
+from paper_1802_10291_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+SYSTEMS = [("identity",), ("hilbert",), ("deriv", 1)]
+PS = [256, 512, 1024, 2048, 4096]
+
+
+def _uneven(seed, batch):
+    rng = S.rng_for(7, seed)
+    cls = rng.integers(0, len(PS), batch).astype(np.int32)
+    cls[:len(PS)] = np.arange(len(PS))
+    in_len = np.array([3 * PS[c] for c in cls])
+    out_len = np.array([4 * PS[c] for c in cls])
+    x = rng.standard_normal(int(in_len.sum()))
+    return cls, in_len, out_len, x
+
+
+def test_autotune_gives_identical_results(cuda_device):
+    cls, in_len, out_len, xh = _uneven(1, 60)
+    x = torch.tensor(xh, dtype=torch.float32, device="cuda")
+    outs, infos = [], []
+    for tune in (False, True):
+        plan = mci.Plan(SYSTEMS, PS, [4 * p for p in PS], max_batch=60, autotune=tune)
+        y = torch.full((int(out_len.sum()),), float("nan"), device="cuda")
+        mci.mci_interp_1d(plan.handle, x, None, y, None, cls, 60)
+        torch.cuda.synchronize()
+        infos.append(plan.info())
+        assert infos[-1]["device_status"] == 0
+        outs.append(y)
+        plan.close()
+    # each signal's arithmetic is independent of how many share a CTA
+    assert torch.equal(outs[0], outs[1])
+    assert all(1 <= g <= 64 for g in infos[1]["signals_per_cta"][:len(PS)])
+    # and both match the oracle on the first signal of every class
+    out_off = np.concatenate([[0], np.cumsum(out_len)[:-1]])
+    in_off = np.concatenate([[0], np.cumsum(in_len)[:-1]])
+    yh = outs[1].cpu().double().numpy()
+    for b in range(len(PS)):
+        P = PS[cls[b]]
+        ref = O.mci_direct(SYSTEMS, xh[in_off[b]:in_off[b] + 3 * P].reshape(1, 3, P), 4 * P)[0, 0]
+        got = yh[out_off[b]:out_off[b] + 4 * P]
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.sqrt(np.mean(ref ** 2))
+
+
+def test_graph_capture_uniform_batch(cuda_device):
+    P, batch = 1024, 300
+    rng = S.rng_for(7, 2)
+    plan = mci.Plan(SYSTEMS, P, 4 * P, max_batch=batch)
+    x = torch.tensor(rng.standard_normal((batch, 3, P)), dtype=torch.float32, device="cuda")
+    y = torch.empty((batch, 1, 4 * P), device="cuda")
+    plan.interp_1d(x, y)                       # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.interp_1d(x, y)
+    x.copy_(torch.tensor(rng.standard_normal((batch, 3, P)), dtype=torch.float32))
+    y.fill_(float("nan"))
+    g.replay()
+    ref = torch.empty_like(y)
+    plan.interp_1d(x, ref)
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    assert torch.equal(y, ref)
+    plan.close()
+
+
+def test_graph_capture_device_grouping(cuda_device):
+    """Size classes in device memory, scratch in the library's static array: the whole
+    uneven step (grouping kernel and its device-side class launches) replays from a graph."""
+    cls, in_len, out_len, xh = _uneven(3, 50)
+    x = torch.tensor(xh, dtype=torch.float32, device="cuda")
+    sc = torch.tensor(cls, device="cuda")
+    plan = mci.Plan(SYSTEMS, PS, [4 * p for p in PS], max_batch=50)
+    y = torch.full((int(out_len.sum()),), float("nan"), device="cuda")
+    mci.mci_interp_1d_noalloc(plan.handle, x, None, y, None, sc, 50)   # warm-up, symbol lookup
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        mci.mci_interp_1d_noalloc(plan.handle, x, None, y, None, sc, 50)
+    y.fill_(float("nan"))
+    g.replay()
+    ref = torch.full_like(y, float("nan"))
+    mci.mci_interp_1d(plan.handle, x, None, ref, None, sc, 50)
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    assert torch.equal(y, ref)
+    plan.close()
