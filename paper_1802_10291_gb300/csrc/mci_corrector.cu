@@ -11,9 +11,9 @@
 // Kernels (CUDA cores, one 16 x 16 pixel tile of one image per CTA):
 //   conv_fwd      out[co] = b[co] + sum_ci sum_taps w[co][ci][t] x[ci](p + d_t), optional
 //                 ReLU, optional residual add;
-//   conv_bwd_data gin[ci] = sum_co sum_taps w[co][ci][t] g[co](p - d_t), g masked by the
-//                 layer's ReLU (the same kernel with the weights transposed and the
-//                 taps reversed);
+//   conv_bwd_data gin[ci] = (sum_co sum_taps w[co][ci][t] g[co](p - d_t)) * (h[ci](p) > 0),
+//                 h the ReLU output of the layer below (the same kernel with the weights
+//                 transposed, the taps reversed and an output mask);
 //   conv_bwd_w    gw[co][ci][t] = sum_p g[co](p) x[ci](p + d_t), gb[co] = sum_p g[co](p),
 //                 per-CTA partial sums reduced with atomics;
 //   mse, adam, image generator.
@@ -47,11 +47,12 @@ __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >=
 // x: [B][cin][H][W]; w: bf16 [COUT][cin][9] (forward) -- when transposed_w, the weights
 // are read as w[ci][co][8 - t] from a [cin_fwd = COUT... ] tensor laid out [cin][COUT][9]
 // (i.e. the forward tensor of the layer whose data gradient this is).
-// mask: optional [B][cin][H][W] ReLU mask source (x *= (mask > 0)).
+// out_mask: optional [B][COUT][H][W]; outputs where out_mask <= 0 are zeroed (the ReLU
+// derivative of the layer below, applied to a data gradient).
 template <int COUT>
 __global__ void __launch_bounds__(kCThreads) conv3x3_kernel(
     const float* __restrict__ x, int cin, const __nv_bfloat16* __restrict__ w, bool transposed_w,
-    const float* __restrict__ bias, const float* __restrict__ mask, const float* __restrict__ res,
+    const float* __restrict__ bias, const float* __restrict__ out_mask, const float* __restrict__ res,
     float* __restrict__ out, int H, int W, bool relu)
 {
     extern __shared__ float csm[];
@@ -64,10 +65,7 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_kernel(
     for (int i = tid; i < cin * kHalo * kHalo; i += kCThreads) {
         const int ci = i / (kHalo * kHalo), r = i % (kHalo * kHalo);
         const int yy = wrap(y0 + r / kHalo - 1, H), xx = wrap(x0 + r % kHalo - 1, W);
-        const int64_t gi = ((int64_t)b * cin + ci) * plane + (int64_t)yy * W + xx;
-        float v = x[gi];
-        if (mask && !(mask[gi] > 0.f)) v = 0.f;
-        xs[i] = v;
+        xs[i] = x[((int64_t)b * cin + ci) * plane + (int64_t)yy * W + xx];
     }
     for (int i = tid; i < cin * 9 * COUT; i += kCThreads) {
         const int ci = i / (9 * COUT), t = (i / COUT) % 9, co = i % COUT;
@@ -109,6 +107,7 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_kernel(
             float v = acc[co];
             if (relu) v = fmaxf(v, 0.f);
             if (res) v += res[o];
+            if (out_mask && !(out_mask[o] > 0.f)) v = 0.f;
             out[o] = v;
         }
     }
@@ -190,16 +189,20 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_wgrad_kernel(
 // operand of tap (dy, dx) is rows (dy + 1) * 32 .. + 127 of copy dx, which
 // starts on a 1024-byte swizzle-atom boundary, so every tap is a plain
 // descriptor offset.  Nine taps x four K = 16 MMAs per tile, issued by one
-// thread; the accumulator (128 lanes x 32 FP32 columns of tensor memory) is
-// read back with tcgen05.ld, one pixel per thread.  Persistent CTAs, two per SM.
+// thread into four partial accumulators (one per K step, so consecutive MMAs are
+// independent), summed when the accumulator (128 lanes x 4 x 32 FP32 columns of
+// tensor memory, two buffers) is read back with tcgen05.ld.  Persistent CTAs of 8
+// warps, two per SM (256 of the 512 tensor-memory columns each).
 // ---------------------------------------------------------------------------
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;
 constexpr int kTcRows = 4, kTcCols = 32;                       // 4 x 32 = 128 MMA rows
 constexpr int kTcHaloRows = kTcRows + 2;
-constexpr int kTcHaloCols = kTcCols + 2;
+constexpr int kTcHaloCols = kTcCols + 2;                       // 6 x 34 = 204 halo pixels
 constexpr int kTcCopyBytes = kTcHaloRows * kTcCols * 128;      // one dx-shifted copy
 constexpr int kTcTapBytes = kWide * 128;                       // one tap's weights
 constexpr int kTcSmem = 3 * kTcCopyBytes + 9 * kTcTapBytes + 1024;
+constexpr int kTcParts = 4;                                    // independent accumulation chains
+constexpr int kTcTmemCols = 2 * kTcParts * 32;                 // two tiles in flight
 
 __device__ __forceinline__ int wrapg(int i, int n)
 {
@@ -212,10 +215,15 @@ __device__ __forceinline__ uint32_t bf16_pair_bits(__nv_bfloat16 a, __nv_bfloat1
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-__global__ void __launch_bounds__(kTcThreads) conv32_tc_kernel(
+// Software pipeline over a CTA's tiles k = 0, 1, ...: stage tile k from registers into
+// the A copies, issue its MMAs into accumulator buffer k mod 2, issue the global loads
+// of tile k + 1 into registers, run the epilogue of tile k - 1 from the other buffer,
+// then wait for tile k's MMAs.  Loads, MMAs and stores of neighbouring tiles overlap.
+// Each of the first 204 threads owns one halo pixel of every tile.
+__global__ void __launch_bounds__(kTcThreads, 2) conv32_tc_kernel(
     const float* __restrict__ x, const __nv_bfloat16* __restrict__ w, bool transposed_w,
-    const float* __restrict__ bias, const float* __restrict__ mask, float* __restrict__ out, int B, int H,
-    int W, bool relu, int* status)
+    const float* __restrict__ bias, const float* __restrict__ out_mask, float* __restrict__ out, int B,
+    int H, int W, bool relu, int* status)
 {
     using namespace mci;
     extern __shared__ __align__(1024) unsigned char tsm_raw[];
@@ -248,9 +256,9 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc_kernel(
         *reinterpret_cast<uint4*>(tap + sw128_offset(co, j * 8)) = q;
         *reinterpret_cast<uint4*>(tap + sw128_offset(co, kWide + j * 8)) = q;
     }
-    if (warp == 0) {
+    if (warp == 0) {   // two buffers of four 32-column partial accumulators
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&tmem_base)), "r"(32) : "memory");
+                     ::"r"(smem_u32(&tmem_base)), "r"(kTcTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
@@ -267,99 +275,134 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc_kernel(
     const int64_t plane = (int64_t)H * W;
     const int tiles_x = (W + kTcCols - 1) / kTcCols, tiles_y = (H + kTcRows - 1) / kTcRows;
     const int n_tiles = B * tiles_y * tiles_x;
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int b = tile / (tiles_y * tiles_x);
+    // threads 0..191: halo rows 0..5 x columns 1..32 (warp w loads row w: every channel
+    // row segment is one aligned 128-byte line); threads 192..203: the edge columns 0, 33
+    const bool has_item = tid < kTcHaloRows * kTcHaloCols;
+    const int r_it = tid < kTcHaloRows * kTcCols ? tid / kTcCols : (tid - kTcHaloRows * kTcCols) >> 1;
+    const int h_it = tid < kTcHaloRows * kTcCols ? tid % kTcCols + 1 : ((tid & 1) ? kTcHaloCols - 1 : 0);
+    auto tile_origin = [&](int tile, int& b, int& y0, int& x0) {
+        b = tile / (tiles_y * tiles_x);
         const int r2 = tile - b * tiles_y * tiles_x;
-        const int y0 = (r2 / tiles_x) * kTcRows, x0 = (r2 % tiles_x) * kTcCols;
-        const float* xb = x + (int64_t)b * kWide * plane;
-        const float* mb = mask ? mask + (int64_t)b * kWide * plane : nullptr;
-        // halo pixel (r, h) = image pixel (y0 - 1 + r, x0 - 1 + h), periodic; it is row
-        // r * 32 + (h - 1 - dx) of copy dx where that index lies in 0..31
-        for (int it = tid; it < kTcHaloRows * kTcHaloCols; it += kTcThreads) {
-            const int r = it / kTcHaloCols, h = it - r * kTcHaloCols;
-            const int64_t pix = (int64_t)wrapg(y0 - 1 + r, H) * W + wrapg(x0 - 1 + h, W);
-            float v[kWide];
+        y0 = (r2 / tiles_x) * kTcRows;
+        x0 = (r2 % tiles_x) * kTcCols;
+    };
+    // halo pixel (r, h) = image pixel (y0 - 1 + r, x0 - 1 + h), periodic
+    float v[kWide];
+    auto load_tile = [&](int tile) {
+        if (!has_item || tile >= n_tiles) return;
+        int b, y0, x0;
+        tile_origin(tile, b, y0, x0);
+        const float* src = x + (int64_t)b * kWide * plane + (int64_t)wrapg(y0 - 1 + r_it, H) * W +
+                           wrapg(x0 - 1 + h_it, W);
 #pragma unroll
-            for (int c = 0; c < kWide; ++c) v[c] = xb[c * plane + pix];
-            if (mb) {
+        for (int c = 0; c < kWide; ++c) v[c] = __ldg(src + c * plane);
+    };
+    // split into hi + lo BF16 and store as row r * 32 + (h - 1 - dx) of copy dx
+    auto stage = [&]() {
+        if (!has_item) return;
+        uint4 hi[4], lo[4];
 #pragma unroll
-                for (int c = 0; c < kWide; ++c)
-                    if (!(mb[c * plane + pix] > 0.f)) v[c] = 0.f;
+        for (int j = 0; j < 4; ++j) {
+            uint32_t ph[4], pl[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c0 = j * 8 + 2 * e;
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(v[c0]), h1 = __float2bfloat16_rn(v[c0 + 1]);
+                ph[e] = bf16_pair_bits(h0, h1);
+                pl[e] = bf16_pair_bits(__float2bfloat16_rn(v[c0] - __bfloat162float(h0)),
+                                       __float2bfloat16_rn(v[c0 + 1] - __bfloat162float(h1)));
             }
-            uint4 hi[4], lo[4];
+            hi[j] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+            lo[j] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                uint32_t ph[4], pl[4];
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int px = h_it - 1 - dx;
+            if (px >= 0 && px < kTcCols) {
+                char* cp = Acp + (dx + 1) * kTcCopyBytes;
+                const int row = r_it * kTcCols + px;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int c0 = j * 8 + 2 * e;
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[c0]), h1 = __float2bfloat16_rn(v[c0 + 1]);
-                    ph[e] = bf16_pair_bits(h0, h1);
-                    pl[e] = bf16_pair_bits(__float2bfloat16_rn(v[c0] - __bfloat162float(h0)),
-                                           __float2bfloat16_rn(v[c0 + 1] - __bfloat162float(h1)));
-                }
-                hi[j] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                lo[j] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-            }
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int px = h - 1 - dx;
-                if (px >= 0 && px < kTcCols) {
-                    char* cp = Acp + (dx + 1) * kTcCopyBytes;
-                    const int row = r * kTcCols + px;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        *reinterpret_cast<uint4*>(cp + sw128_offset(row, j * 8)) = hi[j];
-                        *reinterpret_cast<uint4*>(cp + sw128_offset(row, kWide + j * 8)) = lo[j];
-                    }
+                for (int j = 0; j < 4; ++j) {
+                    *reinterpret_cast<uint4*>(cp + sw128_offset(row, j * 8)) = hi[j];
+                    *reinterpret_cast<uint4*>(cp + sw128_offset(row, kWide + j * 8)) = lo[j];
                 }
             }
         }
+    };
+    // warp w: pixels 32 (w mod 4) .. + 31 (its TMEM lanes), channels 16 (w div 4) .. + 15
+    auto epilogue = [&](int tile, int buf) {
+        int b, y0, x0;
+        tile_origin(tile, b, y0, x0);
+        const int quarter = warp & 3, half = warp >> 2;
+        float acc[16];
+#pragma unroll
+        for (int part = 0; part < kTcParts; ++part) {
+            uint32_t pv[16];
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) +
+                          (uint32_t)(buf * kTcParts * 32 + part * 32 + half * 16),
+                      pv);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = part == 0 ? __uint_as_float(pv[j]) : acc[j] + __uint_as_float(pv[j]);
+        }
+        const int m = quarter * 32 + (tid & 31);
+        const int y = y0 + m / kTcCols, xq = x0 + m % kTcCols;
+        if (y < H && xq < W) {
+            const int64_t o0 = (int64_t)b * kWide * plane + (int64_t)y * W + xq;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int co = half * 16 + j;
+                const int64_t o = o0 + co * plane;
+                float val = acc[j] + (bias ? bias[co] : 0.f);
+                if (relu) val = fmaxf(val, 0.f);
+                if (out_mask && !(out_mask[o] > 0.f)) val = 0.f;
+                out[o] = val;
+            }
+        }
+    };
+
+    uint32_t phase = 0;
+    int k = 0, prev = -1;
+    load_tile(blockIdx.x);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+        stage();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // K step kk (16 of the 64 BF16 of a row) of every tap accumulates into partial
+            // accumulator kk: four independent chains, issued interleaved
+            const uint32_t dst = tmem + (uint32_t)((k & 1) * kTcParts * 32);
 #pragma unroll
             for (int t = 0; t < 9; ++t) {
                 const int dy = t / 3 - 1, dx = t % 3 - 1;
                 const uint32_t a0 = smem_u32(Acp + (dx + 1) * kTcCopyBytes + (dy + 1) * kTcCols * 128);
                 const uint32_t b0 = smem_u32(Bw + t * kTcTapBytes);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)   // K = 16 per MMA: 32 bytes into the 128-byte row
-                    mma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
-                             t > 0 || kk > 0);
+                for (int kk = 0; kk < kTcParts; ++kk)   // K = 16 per MMA: 32 bytes into the row
+                    mma_bf16(dst + kk * 32, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
+                             t > 0);
             }
             mma_commit(smem_u32(&bar));
         }
+        load_tile(tile + gridDim.x);
+        if (prev >= 0) epilogue(prev, (k - 1) & 1);
         if (!mbar_wait(smem_u32(&bar), phase)) {
             atomicOr(status, 1);
             s_abort = 1;
         }
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-            const int y = y0 + tid / kTcCols, xq = x0 + tid % kTcCols;
-            if (!s_abort && y < H && xq < W) {
-                float* ob = out + (int64_t)b * kWide * plane + (int64_t)y * W + xq;
-#pragma unroll
-                for (int co = 0; co < kWide; ++co) {
-                    float val = __uint_as_float(v[co]) + (bias ? bias[co] : 0.f);
-                    if (relu) val = fmaxf(val, 0.f);
-                    ob[co * plane] = val;
-                }
-            }
-        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (s_abort) break;
+        prev = tile;
     }
+    if (prev >= 0 && !s_abort) epilogue(prev, (k - 1) & 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols)
+                     : "memory");
     }
 }
 
@@ -494,23 +537,24 @@ int tc_grid_limit()
     return n;
 }
 
+// out_mask: optional tensor shaped like out; outputs where it is <= 0 are zeroed.
 cudaError_t conv(const float* x, int cin, int cout, const __nv_bfloat16* w, bool tw, const float* bias,
-                 const float* mask, const float* res, float* out, int B, int H, int W, bool relu,
+                 const float* out_mask, const float* res, float* out, int B, int H, int W, bool relu,
                  cudaStream_t s, int* status)
 {
     if (cin == kWide && cout == kWide && !res) {
         const int tiles = B * ((H + kTcRows - 1) / kTcRows) * ((W + kTcCols - 1) / kTcCols);
         const int grid = tiles < tc_grid_limit() ? tiles : tc_grid_limit();
-        conv32_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(x, w, tw, bias, mask, out, B, H, W, relu, status);
+        conv32_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(x, w, tw, bias, out_mask, out, B, H, W, relu, status);
         return cudaGetLastError();
     }
     const dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, B);
     const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cin * 9 * cout);
     if (cout == kWide) {
         cudaFuncSetAttribute(conv3x3_kernel<kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        conv3x3_kernel<kWide><<<grid, kCThreads, smem, s>>>(x, cin, w, tw, bias, mask, res, out, H, W, relu);
+        conv3x3_kernel<kWide><<<grid, kCThreads, smem, s>>>(x, cin, w, tw, bias, out_mask, res, out, H, W, relu);
     } else {
-        conv3x3_kernel<1><<<grid, kCThreads, smem, s>>>(x, cin, w, tw, bias, mask, res, out, H, W, relu);
+        conv3x3_kernel<1><<<grid, kCThreads, smem, s>>>(x, cin, w, tw, bias, out_mask, res, out, H, W, relu);
     }
     return cudaGetLastError();
 }
@@ -551,23 +595,24 @@ cudaError_t forward(mci_corrector_t c, const float* mci, float* pred, int B, int
     return e;
 }
 
-// backward from d pred (in gbuf[0] region as [B][1][H][W]); parameter gradients into grad
+// backward from d pred ([B][1][H][W]); parameter gradients into grad.  g is the gradient
+// with respect to layer l's pre-activation output: the data-gradient conv of layer l
+// zeroes its output where hidden(l - 1) <= 0 (the ReLU derivative of layer l - 1).
 cudaError_t backward(mci_corrector_t c, const float* mci, const float* gpred, int B, int H, int W,
                      cudaStream_t s)
 {
     const int64_t pix = (int64_t)B * H * W;
     cudaError_t e = cudaMemsetAsync(c->grad, 0, sizeof(float) * c->n_params, s);
-    const float* g = gpred;         // gradient w.r.t. layer l's output (pre-mask for hidden layers)
+    const float* g = gpred;
     int gi = 0;
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         const float* x = l == 0 ? mci : hidden(c, l - 1, pix);
-        const float* gmask = l == kLayers - 1 ? nullptr : hidden(c, l, pix);   // ReLU of this layer
-        e = wgrad(l, x, g, gmask, c->grad + c->woff[l], c->grad + c->boff[l], B, H, W, s);
+        e = wgrad(l, x, g, nullptr, c->grad + c->woff[l], c->grad + c->boff[l], B, H, W, s);
         if (l > 0 && e == cudaSuccess) {
-            // gradient w.r.t. layer l's input = hidden(l - 1): conv with transposed, reversed weights
+            // gradient with respect to layer l's input: conv with transposed, reversed weights
             float* gin = c->gbuf[gi];
-            e = conv(g, cout_of(l), cin_of(l), c->wbf + c->woff[l], true, nullptr, gmask, nullptr, gin, B, H,
-                     W, false, s, c->status);
+            e = conv(g, cout_of(l), cin_of(l), c->wbf + c->woff[l], true, nullptr, hidden(c, l - 1, pix), nullptr,
+                     gin, B, H, W, false, s, c->status);
             g = gin;
             gi ^= 1;
         }
