@@ -285,7 +285,7 @@ def images_2d_section(mci, torch, dev, timed, steps):
     return out
 
 
-def corrector_section(torch, dev, timed, train_steps=300):
+def corrector_section(torch, dev, timed, train_steps=300, steps_per_batch=2):
     """Residual corrector on x4 MCI reconstructions of synthetic 1024^2 images: inference on
     a batch of 32, training steps on batches of 4 pairs generated on the fly (HR generated on
     the device, decimated, upsampled by MCI), PSNR of plain MCI and of the trained corrector
@@ -306,7 +306,6 @@ def corrector_section(torch, dev, timed, train_steps=300):
                         "tflop_s": flop / (ms / 1e3) / 1e12, "flop_per_batch": flop}
     src = corrector.PairSource(n_tr, size, s=s_, seed=1)
     x, hr = src.next()
-    steps_per_batch = 2
     t, _ = timed(lambda: net.train_step(x, hr, n_tr, size, size, 1e-3), 5, 1)
     ms_tr = 1e3 * t / 5
     t_gen, _ = timed(src.next, 3, 1)
@@ -353,8 +352,10 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="only the FP32 step (for launch lists under a profiler)")
     ap.add_argument("--no-corrector", action="store_true")
+    ap.add_argument("--pairs", type=int, default=20000,
+                    help="corrector_train case: training pairs (batches of 4, one step each)")
     ap.add_argument("--case", default=None,
-                    choices=["kernel4096", "corrector", "corrector_small", "sisr_s4"],
+                    choices=["kernel4096", "corrector", "corrector_train", "corrector_small", "sisr_s4"],
                     help="profiling case: the P=4096 size-class kernel alone on 3277 signals")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -446,6 +447,11 @@ def main():
         ss = np.full(64, 4, np.int32)
         t, _ = timed(lambda: plan.upsample_2d(lr, hh, hh, ss, hr, 64), args.steps, args.warmup)
         print(json.dumps({"case": args.case, "ms_per_batch": 1e3 * t / args.steps}), flush=True)
+        return
+    if args.case == "corrector_train":
+        # the configured training: --pairs fresh pairs of 1024^2 (x4 MCI), 4 per step
+        print(json.dumps({"case": args.case, **corrector_section(torch, dev, timed, args.pairs // 4, 1)}),
+              flush=True)
         return
     if args.case == "corrector":
         print(json.dumps({"case": args.case, **corrector_section(torch, dev, timed, args.steps)}),
