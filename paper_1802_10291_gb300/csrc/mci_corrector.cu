@@ -500,6 +500,76 @@ __global__ void __launch_bounds__(kCThreads, 2) wgrad32_kernel(const float* __re
     }
 }
 
+// Weight gradient of the 1 -> 32 and 32 -> 1 layers: thread (c, rows) with c = tid % 32 the
+// wide channel keeps the 9 tap sums of pair (c, 0) over rows 2 (tid / 32) .. + 1 of every
+// tile, sliding a 3 x 3 window of x along each row; persistent CTAs, one atomic per sum.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kCThreads, 2) wgrad_narrow_kernel(const float* __restrict__ x,
+                                                                    const float* __restrict__ g,
+                                                                    float* __restrict__ gw,
+                                                                    float* __restrict__ gb, int B, int H,
+                                                                    int W)
+{
+    static_assert((CIN == 1 && COUT == kWide) || (CIN == kWide && COUT == 1), "one narrow side");
+    extern __shared__ float csm[];
+    float* xs = csm;                          // [CIN][18][18]
+    float* gs = csm + CIN * kHalo * kHalo;    // [COUT][16 * 16 + 1]
+    const int tid = threadIdx.x;
+    const int c = tid & 31, rg = tid >> 5;    // wide channel, row pair
+    const int ci = CIN == 1 ? 0 : c, co = COUT == 1 ? 0 : c;
+    const int64_t plane = (int64_t)H * W;
+    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+    const int n_tiles = B * tiles_x * tiles_y;
+    float acc[9], accb = 0.f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int b = tile / (tiles_x * tiles_y);
+        const int r2 = tile - b * tiles_x * tiles_y;
+        const int y0 = (r2 / tiles_x) * kTile, x0 = (r2 % tiles_x) * kTile;
+        __syncthreads();
+        for (int i = tid; i < CIN * kHalo * kHalo; i += kCThreads) {
+            const int cc = i / (kHalo * kHalo), r = i % (kHalo * kHalo);
+            const int yy = wrap(y0 + r / kHalo - 1, H), xx = wrap(x0 + r % kHalo - 1, W);
+            xs[i] = x[((int64_t)b * CIN + cc) * plane + (int64_t)yy * W + xx];
+        }
+        for (int i = tid; i < COUT * kTile * kTile; i += kCThreads) {
+            const int cc = i / (kTile * kTile), r = i % (kTile * kTile);
+            const int yy = y0 + r / kTile, xx = x0 + r % kTile;
+            gs[cc * kGStride + r] =
+                (yy < H && xx < W) ? g[((int64_t)b * COUT + cc) * plane + (int64_t)yy * W + xx] : 0.f;
+        }
+        __syncthreads();
+        const float* xc = xs + ci * kHalo * kHalo;
+        const float* gc = gs + co * kGStride;
+#pragma unroll 1
+        for (int r = rg * 2; r < rg * 2 + 2; ++r) {
+            float win[3][3];
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+                win[dy][1] = xc[(r + dy) * kHalo];
+                win[dy][2] = xc[(r + dy) * kHalo + 1];
+            }
+#pragma unroll 4
+            for (int px = 0; px < kTile; ++px) {
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    win[dy][0] = win[dy][1];
+                    win[dy][1] = win[dy][2];
+                    win[dy][2] = xc[(r + dy) * kHalo + px + 2];
+                }
+                const float gv = gc[r * kTile + px];
+                accb += gv;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc[t] += gv * win[t / 3][t % 3];
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) atomicAdd(&gw[((int64_t)co * CIN + ci) * 9 + t], acc[t]);
+    if (COUT == kWide || c == 0) atomicAdd(&gb[co], accb);
+}
+
 // d pred: grad = 2 (pred - hr) / n, loss += sum (pred - hr)^2 / n
 __global__ void mse_kernel(const float* __restrict__ pred, const float* __restrict__ hr, float* __restrict__ grad,
                            float* __restrict__ loss, int64_t n)
@@ -659,13 +729,19 @@ cudaError_t wgrad(int l, const float* x, const float* g, const float* gmask, flo
     const dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, B);
     const int cin = cin_of(l), cout = cout_of(l);
     const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cout * kGStride);
-    if (cin == 1) {
+    const int tiles = (int)(grid.x * grid.y * grid.z);
+    if (cin == 1 && !gmask) {
+        wgrad_narrow_kernel<1, kWide><<<tiles < tc_grid_limit() ? tiles : tc_grid_limit(), kCThreads, smem, s>>>(
+            x, g, gw, gb, B, H, W);
+    } else if (cout == 1 && !gmask) {
+        wgrad_narrow_kernel<kWide, 1><<<tiles < tc_grid_limit() ? tiles : tc_grid_limit(), kCThreads, smem, s>>>(
+            x, g, gw, gb, B, H, W);
+    } else if (cin == 1) {
         conv3x3_wgrad_kernel<1, kWide><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
     } else if (cout == 1) {
         conv3x3_wgrad_kernel<kWide, 1><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
     } else if (!gmask) {
         cudaFuncSetAttribute(wgrad32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int tiles = (int)(grid.x * grid.y * grid.z);
         const int cap = tc_grid_limit();
         wgrad32_kernel<<<tiles < cap ? tiles : cap, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
     } else {
