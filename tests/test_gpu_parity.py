@@ -245,3 +245,34 @@ def test_upsample_2d_matches_oracle(cuda_device, where):
         pos += s * s * h * w
         check(got, ref, "fp32")
     plan.close()
+
+
+def test_upsample_2d_paper_mode_three_channels(cuda_device):
+    """Section 5.2 with M = 3 systems {f, f', f''} formed from the LR samples by centred
+    differences, scale 3: a 128 x 128 image and rectangular ones (all on the FFT route: the
+    plan keeps M = 3 image classes off the tensor-core route for accuracy)."""
+    systems = [F, D1, D2]
+    shapes = [(128, 128, 3), (24, 48, 3), (48, 24, 3)]
+    sizes = sorted({(w, s * w) for h, w, s in shapes} | {(h, s * h) for h, w, s in shapes})
+    plan = mci.Plan(systems, [p for p, _ in sizes], [t for _, t in sizes], channels="fd",
+                    max_batch=1, max_images=len(shapes),
+                    max_intermediate=sum(h * s * w for h, w, s in shapes))
+    rng = S.rng_for(2, 4)
+    imgs = [rng.random((h, w)) for h, w, s in shapes]
+    lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), dtype=torch.float32, device="cuda")
+    hr_len = [s * s * h * w for h, w, s in shapes]
+    hr = torch.full((sum(hr_len),), float("nan"), device="cuda")
+    hh = np.array([h for h, w, s in shapes], np.int32)
+    ww = np.array([w for h, w, s in shapes], np.int32)
+    ss = np.array([s for h, w, s in shapes], np.int32)
+    plan.upsample_2d(lr, hh, ww, ss, hr, len(shapes))
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    out = hr.cpu().double().numpy()
+    pos = 0
+    for (h, w, s), im in zip(shapes, imgs):
+        ref = O.upsample_2d(im.astype(np.float32).astype(np.float64), s, systems)
+        got = out[pos:pos + s * s * h * w].reshape(s * h, s * w)
+        check(got, ref, "fp32")
+        pos += s * s * h * w
+    plan.close()
