@@ -283,6 +283,26 @@ def upsample_2d(img, scale, systems, policy="pinv", nthreads=0):
     return cols.T
 
 
+def error_bound(coeff_fn, systems, P, N1=None, n_max=None, policy="pinv", rtol=1e-13):
+    """Bound of Eq. (errorestimate) on eps(f, N) by the Cauchy-Schwarz inequality:
+    bound^2 = sum_{n not in band} |a(n)|^2 + M (sum_m Omega_m) sum_{n not in band} sum_m |a(n) b_m(n)|^2,
+    Omega_m = sup over the band of |r_m|^2 (the printed square on Omega read as a slip)."""
+    M = len(systems)
+    N1 = default_n1(M, P) if N1 is None else N1
+    mu = M * P
+    Q, _ = q_table(systems, P, N1, policy, rtol)
+    omega = np.max(np.abs(Q) ** 2, axis=(0, 2))      # Omega_m: sup over residues r and aliases j
+    if n_max is None:
+        n_max = 8 * mu
+    n = np.arange(-n_max, n_max + 1)
+    a = np.asarray(coeff_fn(n), np.complex128)
+    outside = (n < N1) | (n >= N1 + mu)
+    bm = np.stack([multiplier(s, n) for s in systems])
+    s_out = np.sum(np.abs(a[outside]) ** 2)
+    s_ab = np.sum(np.abs(a[outside]) ** 2 * np.sum(np.abs(bm[:, outside]) ** 2, axis=0))
+    return float(np.sqrt(s_out + M * np.sum(omega) * s_ab))
+
+
 def averaged_error(coeff_fn, systems, P, N1=None, n_max=None, policy="pinv", rtol=1e-13):
     """Phase-averaged error eps(f, N) of Eq. (averageerror):
     eps^2 = sum_{n not in band} |a(n)|^2
