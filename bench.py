@@ -311,6 +311,40 @@ def images_2d_section(mci, torch, dev, timed, steps):
     return out
 
 
+def averaged_error_section(mci, torch, dev, timed, steps):
+    """Eq. (averageerror) and the bound of Eq. (errorestimate) for 16384 signals of the
+    P = 256 class of the headline systems, from 2 n_max + 1 = 6145 FP64 Fourier
+    coefficients each (a(n) ~ CN(0, 1) / (1 + |n|)^1.5): HBM-bound on the coefficients."""
+    import oracle
+    P, n_sig = 256, 16384
+    n_max = 4 * 3 * P
+    L = 2 * n_max + 1
+    g = torch.Generator(device=dev)
+    g.manual_seed(1802_10291 + 6)
+    n = torch.arange(-n_max, n_max + 1, device=dev, dtype=torch.float64)
+    c = torch.randn((n_sig, L, 2), generator=g, device=dev, dtype=torch.float64)
+    c = c / (1.0 + n.abs()).pow(1.5).view(1, L, 1)
+    eps = torch.empty(n_sig, dtype=torch.float64, device=dev)
+    bnd = torch.empty(n_sig, dtype=torch.float64, device=dev)
+    plan = mci.Plan(SYSTEMS, P, 4 * P, max_batch=1)
+    nrep = max(10, steps // 10)
+    t, _ = timed(lambda: mci.mci_averaged_error(plan.handle, 0, c, n_max, n_sig, eps, bnd), nrep, 3)
+    ms = 1e3 * t / nrep
+    hbm, _ = peaks()
+    gbs = c.numel() * 8 / (ms / 1e3) / 1e9
+    ch = c[:2].cpu().numpy()
+    rel = []
+    for b in range(2):
+        tab = ch[b, :, 0] + 1j * ch[b, :, 1]
+        fn = lambda k, tab=tab: tab[np.asarray(k) + n_max]
+        ref = oracle.averaged_error(fn, SYSTEMS, P, n_max=n_max)
+        rel.append(abs(float(eps[b]) - ref) / ref)
+    plan.close()
+    return {"signals": n_sig, "P": P, "n_max": n_max, "ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm,
+            "eps_median": float(eps.median()), "bound_over_eps_median": float((bnd / eps).median()),
+            "rel_err_vs_oracle_2_signals": max(rel)}
+
+
 def corrector_section(torch, dev, timed, train_steps=300, steps_per_batch=2):
     """Residual corrector on x4 MCI reconstructions of synthetic 1024^2 images: inference on
     a batch of 32, training steps on batches of 4 pairs generated on the fly (HR generated on
@@ -531,6 +565,7 @@ def main():
     # ---- image workloads (2-D)
     images = images_2d_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
     corr = corrector_section(torch, dev, timed_local) if rank == 0 and not args.no_corrector else None
+    averr = averaged_error_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
 
     # ---- FP64 on the same batch
     plan64, x64, y64, _ = setup("fp64")
@@ -610,6 +645,7 @@ def main():
             "err_vs_oracle": err,
             "images_2d": images,
             "corrector": corr,
+            "averaged_error": averr,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * batch["n_in"] + plan32_stage_bytes,
                     "d2h_bytes_per_step": 4 * batch["n_out"]},

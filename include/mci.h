@@ -238,6 +238,26 @@ mci_status mci_interp_1d_noalloc(mci_plan_t plan, const void* in, const int64_t*
                                  const int64_t* out_off, const int* size_class, int64_t batch,
                                  mci_stream_t stream);
 
+/*
+ * mci_averaged_error -- the phase-averaged approximation error eps(f, N) of Eq.
+ * (averageerror) (Section 4, Theorem (error)) for a batch of signals given by their
+ * Fourier coefficients, and the Cauchy-Schwarz bound of Eq. (errorestimate):
+ *   eps^2 = sum_{n not in I} |a(n)|^2 (1 + sum_{l=1..M} |sum_m r_m(n + (l-k)P) b_m(n)|^2),
+ *   bound^2 = sum_{n not in I} |a(n)|^2 + M (sum_m Omega_m) sum_{n not in I} sum_m |a(n) b_m(n)|^2,
+ * with r_m the plan's per-residue inverse (Eq. (defrm)) of class size_class, k the block
+ * of n and Omega_m = sup_i |r_m(i)|^2 (the bound reads the square on Omega in Eq.
+ * (errorestimate) as a slip: Cauchy-Schwarz gives sum_m Omega_m).  FP64 throughout.
+ *   coeffs  DEVICE, batch x (2 n_max + 1) complex values (re, im interleaved, FP64):
+ *           a(n) for n = -n_max .. n_max; coefficients beyond n_max are taken as 0.
+ *   n_max   must cover the band I of the class.
+ *   eps     DEVICE, batch doubles (output); bound DEVICE, batch doubles or NULL.
+ * Requires measured channels (MCI_CHANNELS_MEASURED) and no MCI_SYS_CUSTOM system
+ * (its multiplier is known only inside the band): otherwise MCI_ERR_INVALID_ARG.
+ * Stream-ordered; the plan's precision does not matter (its FP64 inverses are used).
+ */
+mci_status mci_averaged_error(mci_plan_t plan, int size_class, const double* coeffs, int64_t n_max,
+                              int64_t batch, double* eps, double* bound, mci_stream_t stream);
+
 /* mci_plan_info -- fill *stats; synchronises the plan's last stream to read the
  * device status word, then clears it. */
 mci_status mci_plan_info(mci_plan_t plan, mci_plan_stats* stats);

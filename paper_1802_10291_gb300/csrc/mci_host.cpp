@@ -235,6 +235,11 @@ struct mci_plan_s {
     GemmJob* d_jobs = nullptr;
     int* d_tile0 = nullptr;
     size_t o2_jobs = 0, o2_tile0 = 0;
+    // averaged-error evaluator: per class r_m(N1 + i) (M x mu FP64 complex) and sum of Omega_m
+    std::vector<double> rtab;            // host staging
+    std::vector<int64_t> rtab_off;       // per class offset in complex elements
+    std::vector<double> omega_sum;
+    void* d_rtab = nullptr;
 };
 
 namespace {
@@ -338,6 +343,25 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
         if (st != MCI_OK) return st;
         p->n_singular += inv.n_singular;
         p->max_cond = std::max(p->max_cond, inv.max_cond);
+        // r_m(N1 + j P + r) = Q_r[m][j] (Eq. (defrm)) for the averaged-error evaluator
+        p->rtab_off[c] = (int64_t)(p->rtab.size() / 2);
+        double osum = 0.0;
+        for (int m = 0; m < M; ++m) {
+            double om = 0.0;
+            for (int j = 0; j < M; ++j)
+                for (int r = 0; r < P; ++r) {
+                    const cd q = inv.Q[((size_t)r * M + m) * M + j];
+                    om = std::max(om, std::norm(q));
+                }
+            for (int j = 0; j < M; ++j)
+                for (int r = 0; r < P; ++r) {
+                    const cd q = inv.Q[((size_t)r * M + m) * M + j];
+                    p->rtab.push_back(q.real());
+                    p->rtab.push_back(q.imag());
+                }
+            osum += om;
+        }
+        p->omega_sum[c] = osum;
         ClassDev& cd_ = p->cdev[c];
         if ((W.size() / 2) % 2) push_cpx(W, cd(0.0));  // 16-byte aligned class region
         cd_.w_off = (int64_t)(W.size() / 2);
@@ -665,6 +689,7 @@ mci_status mci_destroy(mci_plan_t p)
     if (p->d_tables) cudaFree(p->d_tables);
     if (p->d_work) cudaFree(p->d_work);
     if (p->d_gemm) cudaFree(p->d_gemm);
+    if (p->d_rtab) cudaFree(p->d_rtab);
     delete p;
     return MCI_OK;
 }
@@ -829,6 +854,8 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
 
     // FP64 tables
     p->gemm_off.assign(n, -1);
+    p->rtab_off.assign(n, 0);
+    p->omega_sum.assign(n, 0.0);
     std::vector<float> W32;
     std::vector<double> W64;
     st = d.precision == MCI_FP64 ? build_tables<double>(p, W64) : build_tables<float>(p, W32);
@@ -892,6 +919,14 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             if (p->gemm_off[c] >= 0) p->d_kmap[c] = (const float*)p->d_gemm + p->gemm_off[c];
         if (e == cudaSuccess) e = (cudaError_t)prepare_gemm();
         p->table_bytes += (int64_t)(sizeof(float) * p->gemm_tab.size());
+    }
+
+    if (e == cudaSuccess && !p->rtab.empty()) {
+        e = cudaMalloc(&p->d_rtab, sizeof(double) * p->rtab.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_rtab, p->rtab.data(), sizeof(double) * p->rtab.size(), cudaMemcpyHostToDevice,
+                                s);
+        p->table_bytes += (int64_t)(sizeof(double) * p->rtab.size());
     }
 
     // workspace
@@ -1088,6 +1123,40 @@ mci_status mci_upsample_2d(mci_plan_t p, const float* lr, const int64_t* lr_off,
                                   hr_off ? nullptr : p->d_hr_pref, p->d_row_cls, p->d_col_cls,
                                   p->d_items, p->d_sched2, rows, cols, s);
     return e ? MCI_ERR_CUDA : MCI_OK;
+}
+
+mci_status mci_averaged_error(mci_plan_t p, int size_class, const double* coeffs, int64_t n_max,
+                              int64_t batch, double* eps, double* bound, mci_stream_t stream)
+{
+    if (!p || batch < 0) return MCI_ERR_INVALID_ARG;
+    if (batch == 0) return MCI_OK;
+    if (!coeffs || !eps || size_class < 0 || size_class >= (int)p->cls.size()) return MCI_ERR_INVALID_ARG;
+    const mci_desc& d = p->desc;
+    if (d.channel_mode != MCI_CHANNELS_MEASURED) return MCI_ERR_INVALID_ARG;
+    for (int m = 0; m < d.M; ++m)
+        if (d.sys[m].kind == MCI_SYS_CUSTOM) return MCI_ERR_INVALID_ARG;   // b(n) known only in the band
+    const HostClass& hc = p->cls[size_class];
+    const int64_t mu = (int64_t)d.M * hc.P;
+    if (n_max < std::max<int64_t>(-hc.N1, hc.N1 + mu - 1)) return MCI_ERR_INVALID_ARG;   // band inside
+    if (batch > 0x7fffffff) return MCI_ERR_UNSUPPORTED_SIZE;
+    ErrArgs a{};
+    a.r = reinterpret_cast<const double2*>(p->d_rtab) + p->rtab_off[size_class];
+    a.coeffs = reinterpret_cast<const double2*>(coeffs);
+    a.eps = eps;
+    a.bound = bound;
+    a.N1 = hc.N1;
+    a.mu = mu;
+    a.n_max = n_max;
+    a.batch = batch;
+    a.M = d.M;
+    a.P = hc.P;
+    for (int m = 0; m < d.M; ++m) {
+        a.kind[m] = d.sys[m].kind;
+        a.order[m] = d.sys[m].order;
+        a.tau[m] = d.sys[m].tau;
+    }
+    a.omega_sum = p->omega_sum[size_class];
+    return launch_averaged_error(a, stream) == 0 ? MCI_OK : MCI_ERR_CUDA;
 }
 
 mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)

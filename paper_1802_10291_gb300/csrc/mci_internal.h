@@ -126,6 +126,20 @@ struct Sched2D {
     int col_count[MCI_MAX_SIZES];
 };
 
+// Arguments of the averaged-error evaluator (Eq. (averageerror), Eq. (errorestimate)).
+struct ErrArgs {
+    const double2* r;        // r_m(N1 + i), m < M, i < mu: r[m * mu + i]
+    const double2* coeffs;   // [batch][2 n_max + 1]: a(n), n = -n_max .. n_max
+    double* eps;             // [batch]
+    double* bound;           // [batch] or NULL
+    int64_t N1, mu, n_max, batch;
+    int M, P;
+    int kind[MCI_MAX_CHANNELS], order[MCI_MAX_CHANNELS];
+    double tau[MCI_MAX_CHANNELS];
+    double omega_sum;        // sum over m of Omega_m = sup_i |r_m(i)|^2
+};
+int launch_averaged_error(const ErrArgs& a, void* stream);
+
 enum KernelMode { kModeUniform = 0, kModeSorted = 1, kModeRows = 2, kModeCols = 3 };
 
 // Arguments of one size-class launch (passed by value).

@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         lib.mci_plan.restype = ctypes.c_int
         lib.mci_interp_1d.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         lib.mci_interp_1d.restype = ctypes.c_int
+        lib.mci_averaged_error.argtypes = [vp, ctypes.c_int, vp, i64, i64, vp, vp, vp]
+        lib.mci_averaged_error.restype = ctypes.c_int
         lib.mci_interp_1d_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         lib.mci_interp_1d_noalloc.restype = ctypes.c_int
         lib.mci_upsample_2d.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
@@ -209,6 +211,13 @@ def mci_plan(desc: mci_desc, stream=None) -> int:
 def mci_interp_1d(plan: int, inp, in_off, out, out_off, size_class, batch: int, stream=None):
     _check(load().mci_interp_1d(plan, _ptr(inp), _ptr(in_off), _ptr(out), _ptr(out_off),
                                 _ptr(size_class), int(batch), _stream(stream)), "mci_interp_1d")
+
+
+def mci_averaged_error(plan: int, size_class: int, coeffs, n_max: int, batch: int, eps, bound=None,
+                       stream=None):
+    """Phase-averaged error eps(f, N) and its bound from Fourier coefficients (device FP64)."""
+    _check(load().mci_averaged_error(plan, int(size_class), _ptr(coeffs), int(n_max), int(batch),
+                                     _ptr(eps), _ptr(bound), _stream(stream)), "mci_averaged_error")
 
 
 def mci_interp_1d_noalloc(plan: int, inp, in_off, out, out_off, size_class, batch: int,
