@@ -340,7 +340,15 @@ def averaged_error_section(mci, torch, dev, timed, steps):
         ref = oracle.averaged_error(fn, SYSTEMS, P, n_max=n_max)
         rel.append(abs(float(eps[b]) - ref) / ref)
     plan.close()
+    # FP64 operations per coefficient outside the band: the Hermitian form b^H G b (M diagonal
+    # terms of 4, M(M-1)/2 off-diagonal of 10), sum |b_m|^2 (3M), |a|^2 and the sums (7)
+    M = len(SYSTEMS)
+    outside = L - M * P
+    flops = n_sig * outside * (4 * M + 10 * M * (M - 1) // 2 + 3 * M + 7)
+    gflops = flops / (ms / 1e3) / 1e9
     return {"signals": n_sig, "P": P, "n_max": n_max, "ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm,
+            "bound": "alu (FP64)", "fp64_gflops": gflops,
+            "fp64_frac_of_nominal_1250_gflops": gflops / 1250.0,
             "eps_median": float(eps.median()), "bound_over_eps_median": float((bnd / eps).median()),
             "rel_err_vs_oracle_2_signals": max(rel)}
 

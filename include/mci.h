@@ -249,7 +249,7 @@ mci_status mci_interp_1d_noalloc(mci_plan_t plan, const void* in, const int64_t*
  * (errorestimate) as a slip: Cauchy-Schwarz gives sum_m Omega_m).  FP64 throughout.
  *   coeffs  DEVICE, batch x (2 n_max + 1) complex values (re, im interleaved, FP64):
  *           a(n) for n = -n_max .. n_max; coefficients beyond n_max are taken as 0.
- *   n_max   must cover the band I of the class.
+ *   n_max   must cover the band I of the class (and stay below 2^29).
  *   eps     DEVICE, batch doubles (output); bound DEVICE, batch doubles or NULL.
  * Requires measured channels (MCI_CHANNELS_MEASURED) and no MCI_SYS_CUSTOM system
  * (its multiplier is known only inside the band): otherwise MCI_ERR_INVALID_ARG.

@@ -4,7 +4,9 @@
 // k the (1-based) block of n, I_k = {N1 + (k-1) P .. N1 + k P - 1}, and the bound of
 // Eq. (errorestimate) from the Cauchy-Schwarz inequality,
 //     eps^2 <= sum_{n outside I} |a(n)|^2 + M (sum_m Omega_m) sum_{n outside I} sum_m |a(n) b_m(n)|^2,
-// Omega_m = sup_i |r_m(i)|^2.  One CTA per signal, threads over n, FP64 throughout.
+// Omega_m = sup_i |r_m(i)|^2.  The inner sum is evaluated as the Hermitian form
+// b(n)^H G_r b(n), G_r[m][m'] = sum_l conj(r_m(N1 + l P + r)) r_m'(N1 + l P + r), r the
+// residue of n (tabulated by the plan).  One CTA per signal, threads over n, FP64.
 #include <cuda_runtime.h>
 
 #include "mci_internal.h"
@@ -20,7 +22,7 @@ __device__ __forceinline__ double2 cmul64(double2 a, double2 b)
 }
 
 // b_m(n) of the systems with a closed form (Eq. (sysfunction))
-__device__ double2 multiplier(int kind, int order, double tau, int64_t n)
+__device__ double2 multiplier(int kind, int order, double tau, int n)
 {
     if (kind == MCI_SYS_DERIV) {
         double2 v = make_double2(1.0, 0.0);
@@ -43,29 +45,33 @@ __global__ void __launch_bounds__(kErrThreads) averaged_error_kernel(const ErrAr
     const int64_t len = 2 * a.n_max + 1;
     const double2* c = a.coeffs + b * len;
     double e2 = 0.0, out2 = 0.0, ab2 = 0.0;
-    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-        const int64_t n = i - a.n_max;
-        const int64_t d = n - a.N1;
-        if (d >= 0 && d < a.mu) continue;                    // inside the band
+    // 32-bit index arithmetic (the host checks that n_max and the band fit in 2^30)
+    const int len32 = (int)len, nmax = (int)a.n_max, n1 = (int)a.N1, mu = (int)a.mu, P = a.P;
+    for (int i = threadIdx.x; i < len32; i += blockDim.x) {
+        const int n = i - nmax;
+        const int d = n - n1;
+        if (d >= 0 && d < mu) continue;                      // inside the band
         const double2 an = c[i];
         const double a2 = an.x * an.x + an.y * an.y;
-        const int64_t kb = d >= 0 ? d / a.P : -((-d + a.P - 1) / a.P);   // floor(d / P) = k - 1
-        const int64_t rr = d - kb * a.P;                     // position inside its block
+        const int kb = d >= 0 ? d / P : -((-d + P - 1) / P);   // floor(d / P) = k - 1
+        const int rr = d - kb * P;                           // position inside its block
         double2 bm[MCI_MAX_CHANNELS];
         double sb2 = 0.0;
         for (int m = 0; m < a.M; ++m) {
             bm[m] = multiplier(a.kind[m], a.order[m], a.tau[m], n);
             sb2 += bm[m].x * bm[m].x + bm[m].y * bm[m].y;
         }
+        // tot = b^H G b = sum_m G_mm |b_m|^2 + 2 Re sum_{m < m'} conj(b_m) G_mm' b_m'
+        const double2* G = a.G + (int64_t)rr * a.M * a.M;
         double tot = 0.0;
-        for (int l = 0; l < a.M; ++l) {                      // n + (l - k) P sits in block l
-            double2 s = make_double2(0.0, 0.0);
-            for (int m = 0; m < a.M; ++m) {
-                const double2 t = cmul64(a.r[(int64_t)m * a.mu + (int64_t)l * a.P + rr], bm[m]);
-                s.x += t.x;
-                s.y += t.y;
+        for (int m = 0; m < a.M; ++m) {
+            tot += G[m * a.M + m].x * (bm[m].x * bm[m].x + bm[m].y * bm[m].y);
+            for (int m2 = m + 1; m2 < a.M; ++m2) {
+                const double2 cb = make_double2(bm[m].x * bm[m2].x + bm[m].y * bm[m2].y,
+                                                bm[m].x * bm[m2].y - bm[m].y * bm[m2].x);   // conj(b_m) b_m'
+                const double2 g = G[m * a.M + m2];
+                tot += 2.0 * (g.x * cb.x - g.y * cb.y);
             }
-            tot += s.x * s.x + s.y * s.y;
         }
         e2 += a2 * (1.0 + tot);
         out2 += a2;

@@ -235,7 +235,8 @@ struct mci_plan_s {
     GemmJob* d_jobs = nullptr;
     int* d_tile0 = nullptr;
     size_t o2_jobs = 0, o2_tile0 = 0;
-    // averaged-error evaluator: per class r_m(N1 + i) (M x mu FP64 complex) and sum of Omega_m
+    // averaged-error evaluator: per class and residue the M x M matrix G_r (FP64 complex)
+    // and the sum of Omega_m
     std::vector<double> rtab;            // host staging
     std::vector<int64_t> rtab_off;       // per class offset in complex elements
     std::vector<double> omega_sum;
@@ -343,22 +344,24 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
         if (st != MCI_OK) return st;
         p->n_singular += inv.n_singular;
         p->max_cond = std::max(p->max_cond, inv.max_cond);
-        // r_m(N1 + j P + r) = Q_r[m][j] (Eq. (defrm)) for the averaged-error evaluator
+        // averaged-error evaluator: with r_m(N1 + l P + r) = Q_r[m][l] (Eq. (defrm)),
+        // sum_l |sum_m r_m(n + (l - k) P) b_m(n)|^2 = b^H G_r b for n in residue r, with
+        // G_r[m][m'] = sum_l conj(Q_r[m][l]) Q_r[m'][l]; stored per r (M x M complex)
         p->rtab_off[c] = (int64_t)(p->rtab.size() / 2);
-        double osum = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int m = 0; m < M; ++m)
+                for (int m2 = 0; m2 < M; ++m2) {
+                    cd acc = 0.0;
+                    for (int l = 0; l < M; ++l)
+                        acc += std::conj(inv.Q[((size_t)r * M + m) * M + l]) * inv.Q[((size_t)r * M + m2) * M + l];
+                    p->rtab.push_back(acc.real());
+                    p->rtab.push_back(acc.imag());
+                }
+        double osum = 0.0;   // sum over m of Omega_m = sup |r_m|^2 (bound of Eq. (errorestimate))
         for (int m = 0; m < M; ++m) {
             double om = 0.0;
             for (int j = 0; j < M; ++j)
-                for (int r = 0; r < P; ++r) {
-                    const cd q = inv.Q[((size_t)r * M + m) * M + j];
-                    om = std::max(om, std::norm(q));
-                }
-            for (int j = 0; j < M; ++j)
-                for (int r = 0; r < P; ++r) {
-                    const cd q = inv.Q[((size_t)r * M + m) * M + j];
-                    p->rtab.push_back(q.real());
-                    p->rtab.push_back(q.imag());
-                }
+                for (int r = 0; r < P; ++r) om = std::max(om, std::norm(inv.Q[((size_t)r * M + m) * M + j]));
             osum += om;
         }
         p->omega_sum[c] = osum;
@@ -1138,9 +1141,10 @@ mci_status mci_averaged_error(mci_plan_t p, int size_class, const double* coeffs
     const HostClass& hc = p->cls[size_class];
     const int64_t mu = (int64_t)d.M * hc.P;
     if (n_max < std::max<int64_t>(-hc.N1, hc.N1 + mu - 1)) return MCI_ERR_INVALID_ARG;   // band inside
-    if (batch > 0x7fffffff) return MCI_ERR_UNSUPPORTED_SIZE;
+    if (batch > 0x7fffffff || n_max >= (1 << 29) || mu >= (1 << 29) || hc.N1 <= -(1 << 29))
+        return MCI_ERR_UNSUPPORTED_SIZE;
     ErrArgs a{};
-    a.r = reinterpret_cast<const double2*>(p->d_rtab) + p->rtab_off[size_class];
+    a.G = reinterpret_cast<const double2*>(p->d_rtab) + p->rtab_off[size_class];
     a.coeffs = reinterpret_cast<const double2*>(coeffs);
     a.eps = eps;
     a.bound = bound;

@@ -128,7 +128,8 @@ struct Sched2D {
 
 // Arguments of the averaged-error evaluator (Eq. (averageerror), Eq. (errorestimate)).
 struct ErrArgs {
-    const double2* r;        // r_m(N1 + i), m < M, i < mu: r[m * mu + i]
+    const double2* G;        // per residue r: G_r[m][m'] = sum_l conj(r_m) r_m' over the M
+                             // aliases, at G[(r * M + m) * M + m']
     const double2* coeffs;   // [batch][2 n_max + 1]: a(n), n = -n_max .. n_max
     double* eps;             // [batch]
     double* bound;           // [batch] or NULL
