@@ -239,6 +239,24 @@ mci_status mci_interp_1d_noalloc(mci_plan_t plan, const void* in, const int64_t*
                                  mci_stream_t stream);
 
 /*
+ * mci_interp_1d_host -- mci_interp_1d on HOST buffers (packed signals): the library
+ * copies the input to the device, interpolates and copies the output back.  The batch
+ * is cut into chunks of consecutive signals (about 32 MB of input each) that move
+ * through three internal streams -- copy in, compute, copy out -- so that transfers in
+ * both directions overlap each other and the compute.
+ *   in, out      HOST, packed as in mci_interp_1d with NULL offsets; page-locked memory
+ *                (cudaHostAlloc / registered) lets the copies run asynchronously.
+ *   size_class   HOST array of batch class indices (NULL for a one-class plan).
+ * The first call (and any call with larger chunks) allocates the chunk buffers (three
+ * slots of input and output) and keeps them with the plan.  Work already queued on
+ * `stream` runs first; the call returns when `out` holds the result (synchronous).
+ * Errors: as mci_interp_1d; MCI_ERR_OOM when the chunk buffers cannot be allocated.
+ * There is no counterpart in the paper.
+ */
+mci_status mci_interp_1d_host(mci_plan_t plan, const void* in, void* out, const int* size_class, int64_t batch,
+                              mci_stream_t stream);
+
+/*
  * mci_averaged_error -- the phase-averaged approximation error eps(f, N) of Eq.
  * (averageerror) (Section 4, Theorem (error)) for a batch of signals given by their
  * Fourier coefficients, and the Cauchy-Schwarz bound of Eq. (errorestimate):

@@ -241,6 +241,12 @@ struct mci_plan_s {
     std::vector<int64_t> rtab_off;       // per class offset in complex elements
     std::vector<double> omega_sum;
     void* d_rtab = nullptr;
+    // host-buffer entry point: chunk buffers and the copy-in / compute / copy-out pipeline
+    static constexpr int kSlots = 3;
+    void* d_chunk = nullptr;             // kSlots x (chunk input | chunk output)
+    size_t chunk_in_bytes = 0, chunk_out_bytes = 0;
+    cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_in[kSlots] = {}, ev_comp[kSlots] = {}, ev_free[kSlots] = {};
 };
 
 namespace {
@@ -693,6 +699,14 @@ mci_status mci_destroy(mci_plan_t p)
     if (p->d_work) cudaFree(p->d_work);
     if (p->d_gemm) cudaFree(p->d_gemm);
     if (p->d_rtab) cudaFree(p->d_rtab);
+    if (p->d_chunk) cudaFree(p->d_chunk);
+    for (cudaStream_t hs : p->hs)
+        if (hs) cudaStreamDestroy(hs);
+    for (int i = 0; i < mci_plan_s::kSlots; ++i) {
+        if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+        if (p->ev_comp[i]) cudaEventDestroy(p->ev_comp[i]);
+        if (p->ev_free[i]) cudaEventDestroy(p->ev_free[i]);
+    }
     delete p;
     return MCI_OK;
 }
@@ -1179,6 +1193,101 @@ mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)
     if (e == cudaSuccess) e = cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
     st->device_status = status;
+    return cuda_status(e);
+}
+
+// Host buffers: packed signals are cut into chunks of consecutive signals (about 32 MB of
+// input each); chunk c uses slot c mod 3 of device buffers and moves through three streams:
+// copy in -> compute (mci_interp_1d, size classes grouped on the host) -> copy out, so the
+// two copy directions and the compute of neighbouring chunks overlap.
+mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int* size_class, int64_t batch,
+                              mci_stream_t stream)
+{
+    if (!p || batch < 0 || batch > p->desc.max_batch) return MCI_ERR_INVALID_ARG;
+    if (batch == 0) return MCI_OK;
+    const int n = (int)p->cls.size();
+    if (!in || !out || (n > 1 && !size_class)) return MCI_ERR_INVALID_ARG;
+    for (int64_t b = 0; b < batch && n > 1; ++b)
+        if (size_class[b] < 0 || size_class[b] >= n) return MCI_ERR_INVALID_ARG;
+    auto in_len = [&](int64_t b) { return (int64_t)p->M_in * p->cls[n > 1 ? size_class[b] : 0].P; };
+    auto out_len = [&](int64_t b) { return (int64_t)p->n_out * p->cls[n > 1 ? size_class[b] : 0].T; };
+    // chunks: consecutive signals up to kChunkIn bytes of input
+    const int64_t kChunkIn = (int64_t)32 << 20;
+    std::vector<int64_t> first{0};
+    std::vector<int64_t> ioff{0}, ooff{0};
+    int64_t cin = 0, cout = 0, max_in = 0, max_out = 0;
+    for (int64_t b = 0; b < batch; ++b) {
+        const int64_t li = in_len(b) * (int64_t)p->elem, lo = out_len(b) * (int64_t)p->elem;
+        if (cin > 0 && cin + li > kChunkIn) {
+            first.push_back(b);
+            ioff.push_back(ioff.back() + cin);
+            ooff.push_back(ooff.back() + cout);
+            cin = cout = 0;
+        }
+        cin += li;
+        cout += lo;
+        max_in = std::max(max_in, cin);
+        max_out = std::max(max_out, cout);
+    }
+    first.push_back(batch);
+    ioff.push_back(ioff.back() + cin);
+    ooff.push_back(ooff.back() + cout);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!p->hs[0]) {
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&p->hs[i], cudaStreamNonBlocking);
+        for (int i = 0; i < mci_plan_s::kSlots && e == cudaSuccess; ++i) {
+            e = cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_comp[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_free[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(p->ev_free[i], p->hs[2]);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    const size_t need_in = align_up((size_t)max_in, 256), need_out = align_up((size_t)max_out, 256);
+    if (need_in > p->chunk_in_bytes || need_out > p->chunk_out_bytes) {
+        e = cudaDeviceSynchronize();
+        if (e == cudaSuccess && p->d_chunk) e = cudaFree(p->d_chunk);
+        p->d_chunk = nullptr;
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_chunk, mci_plan_s::kSlots * (need_in + need_out));
+        if (e != cudaSuccess) {
+            p->chunk_in_bytes = p->chunk_out_bytes = 0;
+            return cuda_status(e);
+        }
+        p->chunk_in_bytes = need_in;
+        p->chunk_out_bytes = need_out;
+    }
+    cudaStream_t s_in = p->hs[0], s_cmp = p->hs[1], s_out = p->hs[2];
+    // the pipeline starts after the caller's prior work on its stream
+    cudaEvent_t ev0 = p->ev_comp[0];
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev0, 0);
+    const int nch = (int)first.size() - 1;
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+        const int slot = c % mci_plan_s::kSlots;
+        char* din = (char*)p->d_chunk + (size_t)slot * (p->chunk_in_bytes + p->chunk_out_bytes);
+        char* dout = din + p->chunk_in_bytes;
+        const int64_t b0 = first[c], nb = first[c + 1] - first[c];
+        e = cudaStreamWaitEvent(s_in, p->ev_free[slot], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(din, (const char*)in + ioff[c], (size_t)(ioff[c + 1] - ioff[c]),
+                                cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[slot], s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cmp, p->ev_in[slot], 0);
+        if (e == cudaSuccess) {
+            const mci_status st = mci_interp_1d(p, din, nullptr, dout, nullptr, n > 1 ? size_class + b0 : nullptr,
+                                                nb, s_cmp);
+            if (st != MCI_OK) return st;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_comp[slot], s_cmp);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, p->ev_comp[slot], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char*)out + ooff[c], dout, (size_t)(ooff[c + 1] - ooff[c]), cudaMemcpyDeviceToHost,
+                                s_out);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_free[slot], s_out);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s_out);
+    p->last_stream = s;
     return cuda_status(e);
 }
 

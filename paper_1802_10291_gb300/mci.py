@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         lib.mci_plan.restype = ctypes.c_int
         lib.mci_interp_1d.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         lib.mci_interp_1d.restype = ctypes.c_int
+        lib.mci_interp_1d_host.argtypes = [vp, vp, vp, vp, i64, vp]
+        lib.mci_interp_1d_host.restype = ctypes.c_int
         lib.mci_averaged_error.argtypes = [vp, ctypes.c_int, vp, i64, i64, vp, vp, vp]
         lib.mci_averaged_error.restype = ctypes.c_int
         lib.mci_interp_1d_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
@@ -211,6 +213,12 @@ def mci_plan(desc: mci_desc, stream=None) -> int:
 def mci_interp_1d(plan: int, inp, in_off, out, out_off, size_class, batch: int, stream=None):
     _check(load().mci_interp_1d(plan, _ptr(inp), _ptr(in_off), _ptr(out), _ptr(out_off),
                                 _ptr(size_class), int(batch), _stream(stream)), "mci_interp_1d")
+
+
+def mci_interp_1d_host(plan: int, inp, out, size_class, batch: int, stream=None):
+    """mci_interp_1d on host buffers (packed), with copies pipelined against the compute."""
+    _check(load().mci_interp_1d_host(plan, _ptr(inp), _ptr(out), _ptr(size_class), int(batch),
+                                     _stream(stream)), "mci_interp_1d_host")
 
 
 def mci_averaged_error(plan: int, size_class: int, coeffs, n_max: int, batch: int, eps, bound=None,

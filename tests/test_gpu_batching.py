@@ -95,3 +95,23 @@ def test_graph_capture_device_grouping(cuda_device):
     assert plan.info()["device_status"] == 0
     assert torch.equal(y, ref)
     plan.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffers_pipeline(cuda_device, pinned):
+    """mci_interp_1d_host: the same results as the device-buffer call, over several chunks
+    (so the three buffer slots are reused)."""
+    cls, in_len, out_len, xh = _uneven(4, 6000)
+    plan = mci.Plan(SYSTEMS, PS, [4 * p for p in PS], max_batch=6000)
+    x = torch.tensor(xh, dtype=torch.float32)
+    y = torch.full((int(out_len.sum()),), float("nan"), dtype=torch.float32)
+    if pinned:
+        x, y = x.pin_memory(), y.pin_memory()
+    mci.mci_interp_1d_host(plan.handle, x, y, cls, 6000)
+    xd = x.cuda()
+    ref = torch.full((int(out_len.sum()),), float("nan"), device="cuda")
+    mci.mci_interp_1d(plan.handle, xd, None, ref, None, cls, 6000)
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    assert torch.equal(y, ref.cpu())
+    plan.close()
