@@ -44,7 +44,7 @@ CPU_PER_CLASS = 100
 # P = 4096, M = 3, T = 16384), from one ncu capture of that launch (3201 signals:
 # 157.65 MB read + 150.64 MB written; profiles/mci_kernel_f32_n2048_p4096.md).
 # None whenever the kernel has changed since the capture.
-ROOFLINE_TRAFFIC_PER_SIGNAL = (157649920 + 150635776) / 3201
+ROOFLINE_TRAFFIC_PER_SIGNAL = None
 
 
 def peaks():

@@ -274,6 +274,34 @@ __device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c
         vec2 = vec2 && ((reinterpret_cast<uintptr_t>(out + off[g]) & 7) == 0);
     }
     const int total = gcount * nout * N;
+    if constexpr (sizeof(R) == 4 && N % 32 == 0) {
+        // s = 4: a warp writes the 256 samples of 32 consecutive l as two fully contiguous
+        // 512-byte stores; lane 2i + e of store h takes component e of l = l0 + 16 h + i
+        // (lanes 2i and 2i + 1 read the same shared-memory words: broadcast)
+        if (vec && s == 4) {
+            const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+            for (int base = (ltid() >> 5) * 32; base < total; base += nwarp * 32) {
+                const int go = base / N;
+                const int l0 = base - go * N;
+                const int g = fastdiv(go, c.mag_nout), o = go - g * nout;
+                const cpx<R>* src0 = sm + g * sst + o * 4 * npad;
+                float* dst = out + off[g] + (int64_t)o * T + (int64_t)8 * l0;
+                const int e = lane & 1;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const cpx<R>* src = src0 + pad16(l0 + 16 * h + (lane >> 1));
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const cpx<R> z = src[u * npad];
+                        v[u] = e ? z.y : z.x;
+                    }
+                    reinterpret_cast<float4*>(dst)[32 * h + lane] = make_float4(v[0], v[1], v[2], v[3]);
+                }
+            }
+            return;
+        }
+    }
     for (int t = ltid(); t < total; t += blockDim.x) {
         const int go = t / N;                    // compile-time N: shift or multiply
         const int l = t - go * N;
