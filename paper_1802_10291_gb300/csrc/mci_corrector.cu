@@ -8,14 +8,15 @@
 // the optimizer), activations and accumulation FP32.  Loss: mean squared error
 // of pred against the HR image.  Training: Adam.
 //
-// Kernels (CUDA cores, one 16 x 16 pixel tile of one image per CTA):
+// Kernels (CUDA cores on 16 x 16 pixel tiles, except the 32 -> 32 convolutions, which
+// run on the tensor cores; see conv32_tc_kernel):
 //   conv_fwd      out[co] = b[co] + sum_ci sum_taps w[co][ci][t] x[ci](p + d_t), optional
 //                 ReLU, optional residual add;
 //   conv_bwd_data gin[ci] = (sum_co sum_taps w[co][ci][t] g[co](p - d_t)) * (h[ci](p) > 0),
 //                 h the ReLU output of the layer below (the same kernel with the weights
 //                 transposed, the taps reversed and an output mask);
 //   conv_bwd_w    gw[co][ci][t] = sum_p g[co](p) x[ci](p + d_t), gb[co] = sum_p g[co](p),
-//                 per-CTA partial sums reduced with atomics;
+//                 register-blocked sums of persistent CTAs reduced with atomics;
 //   mse, adam, image generator.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -109,66 +110,6 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_kernel(
             if (res) v += res[o];
             if (out_mask && !(out_mask[o] > 0.f)) v = 0.f;
             out[o] = v;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// weight gradient: gw[co][ci][t] += sum_p g[co](p) x[ci](p + d_t), gb[co] += sum_p g[co](p)
-// g masked by the layer's ReLU output (gmask) when given.  One CTA per (tile, image);
-// thread t owns (co = t % COUT, ci block of CIB) x 9 taps.
-// ---------------------------------------------------------------------------
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(kCThreads) conv3x3_wgrad_kernel(
-    const float* __restrict__ x, const float* __restrict__ g, const float* __restrict__ gmask,
-    float* __restrict__ gw, float* __restrict__ gb, int H, int W)
-{
-    extern __shared__ float csm[];
-    float* xs = csm;                          // [CIN][18][18]
-    float* gs = csm + CIN * kHalo * kHalo;    // [COUT][16 * 16 + 1]: odd channel stride, so the
-                                              // lanes of a warp (different co) hit different banks
-    const int b = blockIdx.z;
-    const int y0 = blockIdx.y * kTile, x0 = blockIdx.x * kTile;
-    const int tid = threadIdx.x;
-    const int64_t plane = (int64_t)H * W;
-    for (int i = tid; i < CIN * kHalo * kHalo; i += kCThreads) {
-        const int ci = i / (kHalo * kHalo), r = i % (kHalo * kHalo);
-        const int yy = wrap(y0 + r / kHalo - 1, H), xx = wrap(x0 + r % kHalo - 1, W);
-        xs[i] = x[((int64_t)b * CIN + ci) * plane + (int64_t)yy * W + xx];
-    }
-    for (int i = tid; i < COUT * kTile * kTile; i += kCThreads) {
-        const int co = i / (kTile * kTile), r = i % (kTile * kTile);
-        const int yy = y0 + r / kTile, xx = x0 + r % kTile;
-        float v = 0.f;
-        if (yy < H && xx < W) {
-            const int64_t gi = ((int64_t)b * COUT + co) * plane + (int64_t)yy * W + xx;
-            v = g[gi];
-            if (gmask && !(gmask[gi] > 0.f)) v = 0.f;
-        }
-        gs[co * kGStride + r] = v;
-    }
-    __syncthreads();
-    constexpr int PAIRS = CIN * COUT;                     // (co, ci) pairs
-    constexpr int PER = (PAIRS + kCThreads - 1) / kCThreads;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int pr = tid + k * kCThreads;
-        if (pr < PAIRS) {
-            const int co = pr % COUT, ci = pr / COUT;
-            float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            float accb = 0.f;
-            const float* xc = xs + ci * kHalo * kHalo;
-            const float* gc = gs + co * kGStride;
-            for (int p = 0; p < kTile * kTile; ++p) {
-                const float gv = gc[p];
-                const int py = p / kTile, px = p % kTile;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) acc[t] += gv * xc[(py + t / 3) * kHalo + px + t % 3];
-                accb += gv;
-            }
-#pragma unroll
-            for (int t = 0; t < 9; ++t) atomicAdd(&gw[((int64_t)co * CIN + ci) * 9 + t], acc[t]);
-            if (ci == 0) atomicAdd(&gb[co], accb);
         }
     }
 }
@@ -723,31 +664,20 @@ cudaError_t conv(const float* x, int cin, int cout, const __nv_bfloat16* w, bool
     return cudaGetLastError();
 }
 
-cudaError_t wgrad(int l, const float* x, const float* g, const float* gmask, float* gw, float* gb, int B,
-                  int H, int W, cudaStream_t s)
+cudaError_t wgrad(int l, const float* x, const float* g, float* gw, float* gb, int B, int H, int W,
+                  cudaStream_t s)
 {
-    const dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, B);
+    const int tiles = B * ((H + kTile - 1) / kTile) * ((W + kTile - 1) / kTile);
+    const int grid = tiles < tc_grid_limit() ? tiles : tc_grid_limit();
     const int cin = cin_of(l), cout = cout_of(l);
     const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cout * kGStride);
-    const int tiles = (int)(grid.x * grid.y * grid.z);
-    if (cin == 1 && !gmask) {
-        wgrad_narrow_kernel<1, kWide><<<tiles < tc_grid_limit() ? tiles : tc_grid_limit(), kCThreads, smem, s>>>(
-            x, g, gw, gb, B, H, W);
-    } else if (cout == 1 && !gmask) {
-        wgrad_narrow_kernel<kWide, 1><<<tiles < tc_grid_limit() ? tiles : tc_grid_limit(), kCThreads, smem, s>>>(
-            x, g, gw, gb, B, H, W);
-    } else if (cin == 1) {
-        conv3x3_wgrad_kernel<1, kWide><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
+    if (cin == 1) {
+        wgrad_narrow_kernel<1, kWide><<<grid, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
     } else if (cout == 1) {
-        conv3x3_wgrad_kernel<kWide, 1><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
-    } else if (!gmask) {
-        cudaFuncSetAttribute(wgrad32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int cap = tc_grid_limit();
-        wgrad32_kernel<<<tiles < cap ? tiles : cap, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
+        wgrad_narrow_kernel<kWide, 1><<<grid, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
     } else {
-        cudaFuncSetAttribute(conv3x3_wgrad_kernel<kWide, kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        conv3x3_wgrad_kernel<kWide, kWide><<<grid, kCThreads, smem, s>>>(x, g, gmask, gw, gb, H, W);
+        cudaFuncSetAttribute(wgrad32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        wgrad32_kernel<<<grid, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
     }
     return cudaGetLastError();
 }
@@ -782,7 +712,7 @@ cudaError_t backward(mci_corrector_t c, const float* mci, const float* gpred, in
     int gi = 0;
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         const float* x = l == 0 ? mci : hidden(c, l - 1, pix);
-        e = wgrad(l, x, g, nullptr, c->grad + c->woff[l], c->grad + c->boff[l], B, H, W, s);
+        e = wgrad(l, x, g, c->grad + c->woff[l], c->grad + c->boff[l], B, H, W, s);
         if (l > 0 && e == cudaSuccess) {
             // gradient with respect to layer l's input: conv with transposed, reversed weights
             float* gin = c->gbuf[gi];
