@@ -311,6 +311,35 @@ def images_2d_section(mci, torch, dev, timed, steps):
     return out
 
 
+def exactness_section(mci, torch, dev, timed, steps):
+    """One real trig polynomial on the band {-64..63}, M = 2 {f, f'}, P = 64: f and its Hilbert
+    transform at T = 4096 in FP64 and FP32 -- latency of one call and the error against the
+    oracle and against the exact values from the coefficients (Theorem MCIeq)."""
+    from paper_1802_10291_gb300 import synth
+    import oracle
+    systems = [("identity",), ("deriv", 1)]
+    P, T = 64, 4096
+    band = synth.band_of(2, P)
+    a = synth.trig_poly(synth.rng_for(0), band, 1)
+    g = synth.channel_samples(a, band, systems, P)
+    ref = oracle.mci_direct(systems, g, T, outputs=("f", "hilbert"))[0]
+    truth = np.stack([oracle.truth_from_coeffs(a[0], band, T, o) for o in ("f", "hilbert")])
+    out = {}
+    for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        plan = mci.Plan(systems, P, T, outputs=("f", "hilbert"), precision=prec, max_batch=1)
+        x = torch.tensor(g, dtype=dt, device=dev)
+        y = torch.empty((1, 2, T), dtype=dt, device=dev)
+        n = max(50, steps)
+        t, _ = timed(lambda: plan.interp_1d(x, y), n, 3)
+        got = y.cpu().double().numpy()[0]
+        out[prec] = {"us_per_call": 1e6 * t / n,
+                     "max_abs_err_vs_oracle": float(np.max(np.abs(got - ref))),
+                     "max_abs_err_vs_truth": float(np.max(np.abs(got - truth))),
+                     "rms": float(np.sqrt(np.mean(truth ** 2)))}
+        plan.close()
+    return {"config": "M=2 {f, f'}, P=64, band {-64..63}, outputs f and Hf at T=4096", **out}
+
+
 def averaged_error_section(mci, torch, dev, timed, steps):
     """Eq. (averageerror) and the bound of Eq. (errorestimate) for 16384 signals of the
     P = 256 class of the headline systems, from 2 n_max + 1 = 6145 FP64 Fourier
@@ -576,6 +605,7 @@ def main():
     images = images_2d_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
     corr = corrector_section(torch, dev, timed_local) if rank == 0 and not args.no_corrector else None
     averr = averaged_error_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
+    exact = exactness_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
 
     # ---- FP64 on the same batch
     plan64, x64, y64, _ = setup("fp64")
@@ -663,6 +693,7 @@ def main():
             "images_2d": images,
             "corrector": corr,
             "averaged_error": averr,
+            "exactness_m2_p64": exact,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * batch["n_in"] + n_chunks * plan32_stage_bytes,
                     "chunks": n_chunks,
