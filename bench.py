@@ -621,11 +621,11 @@ def main():
         # host buffers through the C ABI: copies in, compute and copies out pipelined in chunks
         mci.mci_interp_1d_host(plan32.handle, h_in, h_out, sc, N_SIGNALS, stream)
 
-    # chunks of the host-buffer call (consecutive signals up to 32 MB of input): each uploads
+    # chunks of the host-buffer call (consecutive signals up to 16 MB of input): each uploads
     # the plan's grouping block once besides its samples
     n_chunks, acc = 1, 0
     for nb in (12 * batch["P"]).tolist():
-        if acc > 0 and acc + nb > (32 << 20):
+        if acc > 0 and acc + nb > (16 << 20):
             n_chunks += 1
             acc = 0
         acc += nb

@@ -241,7 +241,7 @@ mci_status mci_interp_1d_noalloc(mci_plan_t plan, const void* in, const int64_t*
 /*
  * mci_interp_1d_host -- mci_interp_1d on HOST buffers (packed signals): the library
  * copies the input to the device, interpolates and copies the output back.  The batch
- * is cut into chunks of consecutive signals (about 32 MB of input each) that move
+ * is cut into chunks of consecutive signals (about 16 MB of input each) that move
  * through three internal streams -- copy in, compute, copy out -- so that transfers in
  * both directions overlap each other and the compute.
  *   in, out      HOST, packed as in mci_interp_1d with NULL offsets; page-locked memory

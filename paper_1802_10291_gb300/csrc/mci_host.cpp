@@ -1196,7 +1196,7 @@ mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)
     return cuda_status(e);
 }
 
-// Host buffers: packed signals are cut into chunks of consecutive signals (about 32 MB of
+// Host buffers: packed signals are cut into chunks of consecutive signals (about 16 MB of
 // input each); chunk c uses slot c mod 3 of device buffers and moves through three streams:
 // copy in -> compute (mci_interp_1d, size classes grouped on the host) -> copy out, so the
 // two copy directions and the compute of neighbouring chunks overlap.
@@ -1212,7 +1212,7 @@ mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int
     auto in_len = [&](int64_t b) { return (int64_t)p->M_in * p->cls[n > 1 ? size_class[b] : 0].P; };
     auto out_len = [&](int64_t b) { return (int64_t)p->n_out * p->cls[n > 1 ? size_class[b] : 0].T; };
     // chunks: consecutive signals up to kChunkIn bytes of input
-    const int64_t kChunkIn = (int64_t)32 << 20;
+    const int64_t kChunkIn = (int64_t)16 << 20;
     std::vector<int64_t> first{0};
     std::vector<int64_t> ioff{0}, ooff{0};
     int64_t cin = 0, cout = 0, max_in = 0, max_out = 0;
