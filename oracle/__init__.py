@@ -249,6 +249,62 @@ def samples_from_coeffs(coeffs, band, systems, P):
     return np.stack([(E @ (np.asarray(coeffs) * multiplier(s, band))).real for s in systems])
 
 
+def samples_from_coeffs_complex(coeffs, band, systems, P):
+    """Complex channel samples g_m(t_p) = sum_n a(n) b_m(n) e^{i n t_p} of a complex signal."""
+    band = np.asarray(band)
+    tp = 2 * np.pi * np.arange(P) / P
+    E = np.exp(1j * np.outer(tp, band))
+    return np.stack([E @ (np.asarray(coeffs) * multiplier(s, band)) for s in systems])
+
+
+def truth_from_coeffs_complex(coeffs, band, T, op="f"):
+    """sum_n c(n) o(n) e^{2 pi i n j / T}, j < T (complex signal, no real part taken)."""
+    band = np.asarray(band)
+    j = np.arange(T)
+    ph = np.exp(2j * np.pi * np.outer(j, band) / T)
+    return ph @ (np.asarray(coeffs) * out_operator(op, band))
+
+
+def mci_direct_complex(systems, g, T, N1=None, outputs=("f",), policy="pinv", rtol=1e-13):
+    """Sum formula of Theorem MCIeq for complex signals (Examples 4, 5: no real part):
+    out(t_j) = (1/P) sum_m sum_p g_m(t_p) y_m(t_j - t_p), y_m from interp_functions.
+    g: complex [batch, M, P] (or [M, P]); T a multiple of P (t_j - t_p on the T-grid).
+    Returns complex [batch, n_out, T]."""
+    g = np.asarray(g, np.complex128)
+    squeeze = g.ndim == 2
+    if squeeze:
+        g = g[None]
+    batch, M, P = g.shape
+    if T % P:
+        raise ValueError("T must be a multiple of P")
+    s = T // P
+    out = np.zeros((batch, len(outputs), T), np.complex128)
+    j = np.arange(T)
+    for oi, o in enumerate(outputs):
+        Y = interp_functions(systems, P, T, N1=N1, op=o, policy=policy, rtol=rtol)   # [M, T]
+        for m in range(M):
+            for p in range(P):
+                out[:, oi, :] += g[:, m, p:p + 1] * Y[m, (j - p * s) % T][None, :]
+    out /= P
+    return out[0] if squeeze else out
+
+
+def mci_bruteforce_complex(systems, g, T, N1=None, outputs=("f",), rcond=1e-13):
+    """Tiny-P route for complex signals: minimum-norm least-squares solve of
+    sum_{n in band} a(n) b_m(n) e^{i n t_p} = g_m(t_p), then sum_n a(n) o(n) e^{i n t_j}."""
+    g = np.asarray(g, np.complex128)
+    M, P = g.shape
+    N1 = default_n1(M, P) if N1 is None else N1
+    band = np.arange(N1, N1 + M * P)
+    tp = 2 * np.pi * np.arange(P) / P
+    A = np.concatenate([multiplier(sy, band, P, N1)[None, :] * np.exp(1j * np.outer(tp, band))
+                        for sy in systems], axis=0)
+    a, *_ = np.linalg.lstsq(A, g.reshape(-1), rcond=rcond)
+    tj = 2 * np.pi * np.arange(T) / T
+    E = np.exp(1j * np.outer(tj, band))
+    return np.stack([E @ (a * out_operator(o, band)) for o in outputs])
+
+
 def fd_channels(x, systems):
     """Derived channels of Section 5.2: identity -> x, first derivative -> three-point centred
     difference (x[p+1] - x[p-1]) / (2h), second derivative -> (x[p+1] - 2x[p] + x[p-1]) / h^2,
