@@ -311,6 +311,33 @@ def images_2d_section(mci, torch, dev, timed, steps):
     return out
 
 
+def complex_section(mci, torch, dev, timed, steps):
+    """Complex signals (Examples 4, 5): 4096 signals, M = 3 {f, Hf, f'}, P = 1024, T = 4P, FP32
+    complex samples and outputs (no real part taken); realised error against the oracle's
+    complex sum formula on 2 signals."""
+    import oracle
+    P, n_sig = 1024, 4096
+    g = torch.Generator(device=dev)
+    g.manual_seed(1802_10291 + 7)
+    x = torch.randn((n_sig, 3, P, 2), generator=g, device=dev)
+    y = torch.empty((n_sig, 1, 4 * P, 2), device=dev)
+    plan = mci.Plan(SYSTEMS, P, 4 * P, max_batch=n_sig, complex_signal=True)
+    n = max(20, steps // 4)
+    t, _ = timed(lambda: plan.interp_1d(x, y, batch=n_sig), n, 3)
+    ms = 1e3 * t / n
+    byts = (x.numel() + y.numel()) * 4
+    hbm, _ = peaks()
+    xh = x[:2].double().cpu().numpy()
+    ref = oracle.mci_direct_complex(SYSTEMS, xh[..., 0] + 1j * xh[..., 1], 4 * P)[:, 0]
+    got = y[:2, 0].double().cpu().numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    err = float(np.max(np.abs(got - ref)) / np.sqrt(np.mean(np.abs(ref) ** 2)))
+    plan.close()
+    return {"signals": n_sig, "P": P, "T": 4 * P, "ms": ms,
+            "out_msamples_s": n_sig * 4 * P / (ms / 1e3) / 1e6, "gbs": byts / (ms / 1e3) / 1e9,
+            "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm, "fp32_err_over_rms_2_signals": err}
+
+
 def exactness_section(mci, torch, dev, timed, steps):
     """One real trig polynomial on the band {-64..63}, M = 2 {f, f'}, P = 64: f and its Hilbert
     transform at T = 4096 in FP64 and FP32 -- latency of one call and the error against the
@@ -606,6 +633,7 @@ def main():
     corr = corrector_section(torch, dev, timed_local) if rank == 0 and not args.no_corrector else None
     averr = averaged_error_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
     exact = exactness_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
+    cplx = complex_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
 
     # ---- FP64 on the same batch
     plan64, x64, y64, _ = setup("fp64")
@@ -694,6 +722,7 @@ def main():
             "corrector": corr,
             "averaged_error": averr,
             "exactness_m2_p64": exact,
+            "complex_1d": cplx,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * batch["n_in"] + n_chunks * plan32_stage_bytes,
                     "chunks": n_chunks,

@@ -128,6 +128,16 @@ typedef struct {
                                 during the call) and keeps the fastest.  Results do not
                                 depend on G; plan creation takes longer (milliseconds per
                                 class).  There is no counterpart in the paper.           */
+    int complex_signal;      /* 0: real signals; samples and outputs are real, the output is
+                                the real part of the interpolant (Section 5.1 examples).
+                                1: complex signals (Examples 4, 5): samples and outputs are
+                                complex, interleaved (re, im) in the precision's type, input
+                                [M][P] complex per signal, output [n_out][T] complex, and no
+                                real part is taken.  Requires MCI_CHANNELS_MEASURED and no
+                                2-D (max_images = 0); P a power of two up to 4096 or 3 * 2^a
+                                from 6 to 3072, and one signal's max(M, s * n_out) buffers of
+                                P complex values must fit in shared memory (else
+                                MCI_ERR_UNSUPPORTED_SIZE; e.g. FP64 M = 3, s = 2, P = 4096). */
 } mci_desc;
 
 typedef struct {

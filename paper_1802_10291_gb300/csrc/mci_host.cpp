@@ -148,6 +148,21 @@ mci_status invert_residues(const mci_desc& d, int P, int64_t N1, const double* c
     return MCI_OK;
 }
 
+// Complex signals use a length-P complex FFT (no packing): P must be a kernel FFT length.
+bool supported_complex_p(int P)
+{
+    if (P < 2) return false;
+    int q = P;
+    bool three = false;
+    if (q % 3 == 0) {
+        q /= 3;
+        three = true;
+    }
+    if (q & (q - 1)) return false;
+    if (three) return P >= 6 && P <= 3072;
+    return P <= 4096;
+}
+
 bool supported_p(int P)
 {
     if (P < 4 || P % 2) return false;
@@ -281,8 +296,12 @@ mci_status validate(const mci_desc* d)
                 return MCI_ERR_INVALID_ARG;
         }
     }
+    if (d->complex_signal != 0 && d->complex_signal != 1) return MCI_ERR_INVALID_ARG;
+    if (d->complex_signal && (d->channel_mode != MCI_CHANNELS_MEASURED || d->max_images > 0))
+        return MCI_ERR_INVALID_ARG;
     for (int c = 0; c < d->n_sizes; ++c) {
-        if (!supported_p(d->P[c])) return MCI_ERR_UNSUPPORTED_SIZE;
+        if (!(d->complex_signal ? supported_complex_p(d->P[c]) : supported_p(d->P[c])))
+            return MCI_ERR_UNSUPPORTED_SIZE;
         if (d->T[c] < d->P[c] || d->T[c] % d->P[c]) return MCI_ERR_UNSUPPORTED_SIZE;
         for (int c2 = 0; c2 < c; ++c2)
             if (d->P[c2] == d->P[c] && d->T[c2] == d->T[c] &&
@@ -390,6 +409,18 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
         const bool gemm = gemm_eligible(p, hc);
         std::vector<cd> w1;  // single-input-channel weights per bin, phase (GEMM matrix)
         if (gemm) w1.assign((size_t)(N + 1) * Q, 0.0);
+        if (d.complex_signal) {
+            // complex signals: every bin k < P on its own, no symmetrisation; plane (m, q)
+            // holds W[k][m][q] = Wfull(residue of k, m, q) for k = 0..P-1
+            std::vector<cd> cplanes((size_t)Min * Q * P);
+            for (int k = 0; k < P; ++k) {
+                const int r = res(k);
+                for (int m = 0; m < Min; ++m)
+                    for (int q = 0; q < Q; ++q) cplanes[((size_t)m * Q + q) * P + k] = Wfull(r, m, q);
+            }
+            for (const cd& z : cplanes) push_cpx(W, z);
+            continue;
+        }
         // stored as planes: plane (m, q) holds W[k][m][q] for k = 0..N contiguously, so the
         // threads of a warp (consecutive bins) read consecutive elements of a plane
         std::vector<cd> planes((size_t)Min * Q * (N + 1));
@@ -472,8 +503,8 @@ static mci_status interp_1d_host_grouped(mci_plan_t p, KArgs a, const int* size_
         sorted[pos[c]++] = b;
         in_pref[b] = pin;
         out_pref[b] = pout;
-        pin += (int64_t)p->cdev[c].M_in * p->cdev[c].P;
-        pout += (int64_t)p->cdev[c].n_out * p->cdev[c].T;
+        pin += p->cdev[c].in_len;
+        pout += p->cdev[c].out_len;
     }
     cudaError_t e = cudaMemcpyAsync(p->d_sorted, blk, p->stage_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev, s);
@@ -731,7 +762,7 @@ static cudaError_t autotune_tiles(mci_plan_s* p, int smem_cap, cudaStream_t s)
         ClassDev cd = p->cdev[c];
         const int per = cd.sstride * csz;
         const int twb = smem_twiddle_count(cd.N) * csz;
-        const int64_t sig_bytes = (int64_t)(cd.M_in * cd.P + cd.n_out * cd.T) * p->elem;
+        const int64_t sig_bytes = (cd.in_len + cd.out_len) * (int64_t)p->elem;
         const int64_t nsig = std::max<int64_t>(1, std::min<int64_t>((int64_t)scratch_bytes / sig_bytes, 8192));
         std::vector<int> cand;
         for (int budget : {16 << 10, 24 << 10, 32 << 10, 48 << 10, 64 << 10, 96 << 10, 144 << 10}) {
@@ -749,7 +780,7 @@ static cudaError_t autotune_tiles(mci_plan_s* p, int smem_cap, cudaStream_t s)
             a.mode = kModeUniform;
             a.W = p->launch[c].W;
             a.in = scratch;
-            a.out = (char*)scratch + nsig * (int64_t)cd.M_in * cd.P * p->elem;
+            a.out = (char*)scratch + nsig * cd.in_len * (int64_t)p->elem;
             a.batch = nsig;
             a.status = p->d_status;
             const int64_t items = (nsig + G - 1) / G;
@@ -825,7 +856,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         hc.P = desc->P[c];
         hc.T = desc->T[c];
         hc.s = hc.T / hc.P;
-        hc.N = hc.P / 2;
+        hc.N = d.complex_signal ? hc.P : hc.P / 2;   // complex FFT length
         hc.N1 = desc->N1 ? desc->N1[c] : -(int64_t)((int64_t)d.M * hc.P / 2);
         Pmax = std::max(Pmax, hc.P);
         Tmax = std::max(Tmax, hc.T);
@@ -843,6 +874,10 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         cd_.mag_min = fastdiv_magic(cd_.M_in);
         cd_.mag_q = fastdiv_magic(cd_.Q);
         cd_.mag_nout = fastdiv_magic(cd_.n_out);
+        cd_.cplx = d.complex_signal;
+        cd_.chan_len = hc.P * (d.complex_signal ? 2 : 1);
+        cd_.in_len = (int64_t)cd_.M_in * cd_.chan_len;
+        cd_.out_len = (int64_t)cd_.n_out * hc.T * (d.complex_signal ? 2 : 1);
         const int per = cd_.sstride * csz + smem_twiddle_count(hc.N) * csz;
         if (per > smem_cap) {
             delete p;
@@ -1209,8 +1244,8 @@ mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int
     if (!in || !out || (n > 1 && !size_class)) return MCI_ERR_INVALID_ARG;
     for (int64_t b = 0; b < batch && n > 1; ++b)
         if (size_class[b] < 0 || size_class[b] >= n) return MCI_ERR_INVALID_ARG;
-    auto in_len = [&](int64_t b) { return (int64_t)p->M_in * p->cls[n > 1 ? size_class[b] : 0].P; };
-    auto out_len = [&](int64_t b) { return (int64_t)p->n_out * p->cls[n > 1 ? size_class[b] : 0].T; };
+    auto in_len = [&](int64_t b) { return p->cdev[n > 1 ? size_class[b] : 0].in_len; };
+    auto out_len = [&](int64_t b) { return p->cdev[n > 1 ? size_class[b] : 0].out_len; };
     // chunks: consecutive signals up to kChunkIn bytes of input
     const int64_t kChunkIn = (int64_t)16 << 20;
     std::vector<int64_t> first{0};

@@ -77,6 +77,10 @@ struct ClassDev {
                  // signals start on different banks (16-byte aligned)
     int64_t w_off;   // offset of this class's bin weights W[k][m][q], k = 0..N
     uint64_t mag_min, mag_q, mag_nout;   // fastdiv_magic of M_in, Q and n_out
+    int cplx;            // complex signals: FFT length N = P, complex samples and outputs
+    int chan_len;        // reals per input channel: P, or 2 P for complex signals
+    int64_t in_len;      // reals per signal: M_in * chan_len
+    int64_t out_len;     // reals per signal: n_out * T (x 2 for complex signals)
 };
 
 // Device-built grouping of one mci_interp_1d call (uneven batches).

@@ -53,14 +53,14 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
                 const int64_t b = a.mode == kModeSorted
                                       ? a.sorted[a.sched1->start[a.cls] + (int64_t)item * G + g]
                                       : (int64_t)item * G + g;
-                s_in[g] = a.in_off ? a.in_off[b] : b * (int64_t)c.M_in * c.P;
-                s_out[g] = a.out_off ? a.out_off[b] : b * (int64_t)c.n_out * c.T;
+                s_in[g] = a.in_off ? a.in_off[b] : b * c.in_len;
+                s_out[g] = a.out_off ? a.out_off[b] : b * c.out_len;
             }
         }
         __syncthreads();
         // signals whose complex pairs are 8-byte aligned are read by the first FFT pass
         // directly; others are staged in shared memory first
-        bool direct = (c.P % 2) == 0;
+        bool direct = c.cplx || (c.P % 2) == 0;
         for (int g = 0; g < cnt; ++g)
             direct = direct && ((reinterpret_cast<uintptr_t>(static_cast<const R*>(a.in) + s_in[g]) &
                                  (2 * sizeof(R) - 1)) == 0);
@@ -71,7 +71,8 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
             __syncthreads();
             compute_tile<R, N>(sm, c, cnt, W);
         }
-        store_contig<R, N>(sm, c, static_cast<R*>(a.out), s_out, cnt);
+        if (c.cplx) store_contig_complex<R, N>(sm, c, static_cast<R*>(a.out), s_out, cnt);
+        else store_contig<R, N>(sm, c, static_cast<R*>(a.out), s_out, cnt);
         __syncthreads();
     }
 }

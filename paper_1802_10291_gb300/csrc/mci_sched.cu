@@ -104,11 +104,11 @@ sched_1d_kernel(const int* __restrict__ size_class, int64_t batch, int n_classes
             const int c = b < batch ? size_class[b] : -1;
             const bool ok = c >= 0 && c < n_classes;
             int64_t ex;
-            const int64_t tin = block_exclusive_scan(ok ? (int64_t)cl[c].c.M_in * cl[c].c.P : 0, &ex);
+            const int64_t tin = block_exclusive_scan(ok ? cl[c].c.in_len : 0, &ex);
             if (b < batch && in_pref) in_pref[b] = carry_in + ex;
             carry_in += tin;
             const int64_t tout =
-                block_exclusive_scan(ok ? (int64_t)cl[c].c.n_out * cl[c].c.T : 0, &ex);
+                block_exclusive_scan(ok ? cl[c].c.out_len : 0, &ex);
             if (b < batch && out_pref) out_pref[b] = carry_out + ex;
             carry_out += tout;
         }

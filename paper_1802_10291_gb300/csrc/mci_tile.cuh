@@ -159,6 +159,42 @@ __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int 
     else combine_loop<R, 0, 0>(sm, c, gcount, W);
 }
 
+// Complex signals (Examples 4, 5): every bin k < P is its own residue class, so
+// Y_q[k] = sum_m X_m[k] W_m,q[k] with the weights as planes of P bins (no real-input
+// unpacking and no Hermitian packing).  Items (k, g), g fastest.
+template <typename R>
+__device__ __forceinline__ void combine_complex(cpx<R>* sm, const ClassDev& c, int gcount,
+                                                const cpx<R>* __restrict__ W)
+{
+    const int N = c.N, npad = c.npad, sst = c.sstride, Min = c.M_in, Q = c.Q;
+    const int total = N * gcount;
+    const int it0 = ltid();
+    const int step = blockDim.x;
+    const int dk = step / gcount, dg = step - dk * gcount;
+    int k = it0 / gcount, g = it0 - k * gcount;
+    for (int it = it0; it < total; it += step) {
+        cpx<R>* base = sm + g * sst;
+        const int pk = pad16(k);
+        cpx<R> X[MCI_MAX_CHANNELS];
+#pragma unroll
+        for (int m = 0; m < MCI_MAX_CHANNELS; ++m)
+            if (m < Min) X[m] = base[m * npad + pk];
+        for (int q = 0; q < Q; ++q) {
+            cpx<R> y = mk<R>(0, 0);
+#pragma unroll
+            for (int m = 0; m < MCI_MAX_CHANNELS; ++m)
+                if (m < Min) y = y + cmul(X[m], ldw(&W[(m * Q + q) * N + k]));
+            base[q * npad + pk] = y;
+        }
+        k += dk;
+        g += dg;
+        if (g >= gcount) {
+            g -= gcount;
+            ++k;
+        }
+    }
+}
+
 // Buffer f of a tile with `cnt` transforms per signal: signal f / cnt, slot f % cnt.
 struct SlotBase {
     int cnt, sstride, npad;
@@ -181,7 +217,7 @@ struct SrcContig {
     __device__ __forceinline__ const cpx<R>* operator()(int f) const
     {
         const int g = fastdiv(f, mag);
-        return reinterpret_cast<const cpx<R>*>(in + off[g] + (int64_t)(f - g * Min) * P);
+        return reinterpret_cast<const cpx<R>*>(in + off[g] + (int64_t)(f - g * Min) * P);   // P: reals per channel
     }
 };
 
@@ -199,12 +235,13 @@ __device__ __forceinline__ void compute_tile(cpx<R>* sm, const ClassDev& c, int 
     if (gin) {
         // the twiddles are computed while the first pass's global loads are in flight
         fft_many_ct<R, N, false, true>(sm, gcount * c.M_in, SlotBase{c.M_in, c.sstride, c.npad, c.mag_min}, stw,
-                                       SrcContig<R>{gin, s_in, c.M_in, c.P, c.mag_min}, fill);
+                                       SrcContig<R>{gin, s_in, c.M_in, c.chan_len, c.mag_min}, fill);
     } else {
         fill();
         fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.sstride, c.npad, c.mag_min}, stw);
     }
-    combine_tile<R>(sm, c, gcount, W);
+    if (c.cplx) combine_complex<R>(sm, c, gcount, W);
+    else combine_tile<R>(sm, c, gcount, W);
     __syncthreads();
     fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.sstride, c.npad, c.mag_q}, stw);
 }
@@ -231,7 +268,7 @@ template <typename R>
 __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const R* __restrict__ in,
                                             const int64_t* off, int gcount)
 {
-    const int P = c.P, Min = c.M_in, npad = c.npad, sst = c.sstride;
+    const int P = c.chan_len, Min = c.M_in, npad = c.npad, sst = c.sstride;   // P: reals per channel
     const int per = Min * P;
     constexpr int VW = sizeof(R) == 4 ? 4 : 2;  // reals per 16-byte copy
     bool vec = (P % VW) == 0;
@@ -332,6 +369,36 @@ __device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c
                 const cpx<R> z = src[u * npad];
                 dst[u] = z.x;
                 dst[s + u] = z.y;
+            }
+        }
+    }
+}
+
+// Complex outputs: output o of signal g at out + off[g] + 2 o T (interleaved re, im);
+// sample j = s l + u is element l of phase buffer (o, u), so one thread per (g, o, l)
+// writes the s consecutive complex samples [s l, s l + s).
+template <typename R, int N>
+__device__ __forceinline__ void store_contig_complex(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
+                                                     const int64_t* off, int gcount)
+{
+    const int T = c.T, s = c.s, npad = c.npad, sst = c.sstride, nout = c.n_out;
+    bool vec = true;   // complex values as 8-byte (FP32) or 16-byte (FP64) stores
+    for (int g = 0; g < gcount; ++g)
+        vec = vec && ((reinterpret_cast<uintptr_t>(out + off[g]) & (2 * sizeof(R) - 1)) == 0);
+    const int total = gcount * nout * N;
+    for (int t = ltid(); t < total; t += blockDim.x) {
+        const int go = t / N;
+        const int l = t - go * N;
+        const int g = fastdiv(go, c.mag_nout), o = go - g * nout;
+        const cpx<R>* src = sm + g * sst + o * s * npad + pad16(l);
+        R* dst = out + off[g] + 2 * ((int64_t)o * T + (int64_t)s * l);
+        for (int u = 0; u < s; ++u) {
+            const cpx<R> z = src[u * npad];
+            if (vec) {
+                *reinterpret_cast<cpx<R>*>(dst + 2 * u) = z;
+            } else {
+                dst[2 * u] = z.x;
+                dst[2 * u + 1] = z.y;
             }
         }
     }

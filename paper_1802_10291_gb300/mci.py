@@ -60,7 +60,8 @@ class mci_desc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("singular_policy", ctypes.c_int),
                 ("singular_rtol", ctypes.c_double), ("channel_mode", ctypes.c_int),
                 ("max_batch", ctypes.c_int64), ("max_images", ctypes.c_int64),
-                ("max_intermediate", ctypes.c_int64), ("autotune", ctypes.c_int)]
+                ("max_intermediate", ctypes.c_int64), ("autotune", ctypes.c_int),
+                ("complex_signal", ctypes.c_int)]
 
 
 class mci_plan_stats(ctypes.Structure):
@@ -159,7 +160,7 @@ def _stream(stream):
 
 def make_desc(systems, P, T, N1=None, outputs=("f",), precision="fp32", singular="pinv",
               singular_rtol=0.0, channels="measured", max_batch=1, max_images=0,
-              max_intermediate=0, autotune=False):
+              max_intermediate=0, autotune=False, complex_signal=False):
     """Build an mci_desc (plus the arrays it points to, kept alive on the returned object).
     systems: list of ('identity',), ('deriv', k), ('hilbert',), ('shift', tau), ('custom', table)
     where table is a float64 array of 2*M*P_c values per size class, concatenated."""
@@ -199,6 +200,7 @@ def make_desc(systems, P, T, N1=None, outputs=("f",), precision="fp32", singular
     d.max_images = int(max_images)
     d.max_intermediate = int(max_intermediate)
     d.autotune = 1 if autotune else 0
+    d.complex_signal = 1 if complex_signal else 0
     d._keep = (sysarr, Parr, Tarr, N1arr, keep)
     return d
 
