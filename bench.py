@@ -259,8 +259,7 @@ def images_2d_section(mci, torch, dev, timed, steps):
             "err_vs_oracle_image0": err}
         plan.close()
     # --- Section 5.2 with M = 2 {f, f'} and M = 3 {f, f', f''} (centred differences), scale 3:
-    # 16 synthetic 768^2 images decimated to 256^2 (P = 256, T = 768: tensor-core route for
-    # M = 2, FFT route for M = 3)
+    # 16 synthetic 768^2 images decimated to 256^2 (P = 256, T = 768: FFT route)
     n3 = 16
     rng = synth.rng_for(2, 1)
     hr3 = np.stack([synth.synthetic_image(rng, 768) for _ in range(n3)]).astype(np.float32)

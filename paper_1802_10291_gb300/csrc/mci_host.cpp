@@ -335,16 +335,19 @@ void push_cpx(std::vector<R>& v, cd z)
 // Image size classes small enough for the tensor-core path: the T x P matrix of the
 // linear map is formed by the plan, and both passes of an image run as GEMMs when
 // its row and column classes are both eligible.
-// Image classes served by the tensor-core route.  Its FP32 accumulation error (two
-// passes of length-P dot products on the tensor cores) is several times that of the
-// FFT route: measured on a 256^2 -> 768^2 image, 4.4e-6 x RMS with M = 2 systems
-// {f, f'} but 1.06e-5 x RMS with M = 3 {f, f', f''} (over the 1e-5 FP32 tolerance;
-// the FFT route gives 1.0e-6 per pass for both), so it takes M <= 2 only.
+// Image classes served by the tensor-core route (two dense products per image).  Its work
+// grows with P * T while the FFT route's grows with T log P; measured per batch (GEMM vs
+// FFT route, M = 2): 64 x 128^2 x2 0.055 vs 0.073 ms, 64 x 128^2 x4 0.111 vs 0.115 ms,
+// 64 x 256^2 x2 0.226 vs 0.152 ms, 16 x 256^2 x3 0.133 vs 0.093 ms, 32 x 256^2 x4 0.349 vs
+// 0.202 ms -- so it takes P = 128 with T <= 512 only.  Its FP32 accumulation error is
+// also several times that of the FFT route: 4.4e-6 x RMS with M = 2 systems {f, f'} but
+// 1.06e-5 x RMS with M = 3 {f, f', f''} (over the 1e-5 FP32 tolerance; the FFT route gives
+// 1.0e-6 per pass) on a 256^2 -> 768^2 image, so it takes M <= 2 only.
 bool gemm_eligible(const mci_plan_s* p, const HostClass& hc)
 {
     const mci_desc& d = p->desc;
     return d.max_images > 0 && d.precision == MCI_FP32 && p->M_in == 1 && d.M <= 2 && p->n_out == 1 &&
-           hc.P % 128 == 0 && hc.P <= 256 && hc.T % 128 == 0 && hc.T <= 2048;
+           hc.P == 128 && hc.T % 128 == 0 && hc.T <= 512;
 }
 
 template <typename R>

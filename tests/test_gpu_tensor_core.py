@@ -1,5 +1,5 @@
-"""The tensor-core image path: for size classes with P in {128, 256}
-the row and column passes run as tcgen05 GEMMs with split-BF16 operands (six products,
+"""The tensor-core image path: for size classes with P = 128 and T <= 512 (where it beats
+the FFT route) the row and column passes run as tcgen05 GEMMs with split-BF16 operands (six products,
 FP32 accumulation).  Checked against the FP64 oracle (Section 5.2 separable
 interpolation) and against the FFT path on the same images."""
 import numpy as np
