@@ -132,10 +132,12 @@ __global__ void __launch_bounds__(kCThreads) conv3x3_kernel(
 // descriptor offset.  Nine taps x four K = 16 MMAs per tile, issued by one
 // thread into four partial accumulators (one per K step, so consecutive MMAs are
 // independent), summed when the accumulator (128 lanes x 4 x 32 FP32 columns of
-// tensor memory, two buffers) is read back with tcgen05.ld.  Persistent CTAs of 8
-// warps, two per SM (256 of the 512 tensor-memory columns each).
+// tensor memory, two buffers) is read back with tcgen05.ld.  Persistent CTAs of 9
+// warps (8 stage and store, one issues the MMAs), two per SM (256 of the 512
+// tensor-memory columns each).
 // ---------------------------------------------------------------------------
-constexpr int kTcThreads = 256;
+constexpr int kTcWorkers = 256;                              // staging and epilogue warps 0..7
+constexpr int kTcThreads = kTcWorkers + 32;                  // + warp 8: issues the MMAs
 constexpr int kTcRows = 4, kTcCols = 32;                       // 4 x 32 = 128 MMA rows
 constexpr int kTcHaloRows = kTcRows + 2;
 constexpr int kTcHaloCols = kTcCols + 2;                       // 6 x 34 = 204 halo pixels
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv32_tc_kernel(
         stage();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
+        if (tid == kTcWorkers) {   // lane 0 of the MMA warp, which has no other work
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // K step kk (16 of the 64 BF16 of a row) of every tap accumulates into partial
             // accumulator kk: four independent chains, issued interleaved
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv32_tc_kernel(
             mma_commit(smem_u32(&bar));
         }
         load_tile(tile + gridDim.x);
-        if (prev >= 0) epilogue(prev, (k - 1) & 1);
+        if (prev >= 0 && warp < kTcWorkers / 32) epilogue(prev, (k - 1) & 1);
         if (!mbar_wait(smem_u32(&bar), phase)) {
             atomicOr(status, 1);
             s_abort = 1;
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv32_tc_kernel(
         if (s_abort) break;
         prev = tile;
     }
-    if (prev >= 0 && !s_abort) epilogue(prev, (k - 1) & 1);
+    if (prev >= 0 && !s_abort && warp < kTcWorkers / 32) epilogue(prev, (k - 1) & 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
