@@ -42,9 +42,9 @@ CPU_PER_CLASS = 100
 
 # DRAM bytes (read + write) per signal of the timed roofline kernel (mci_kernel<float, 2048>,
 # P = 4096, M = 3, T = 16384), from one ncu capture of that launch (3201 signals:
-# 157.68 MB read + 152.13 MB written; profiles/mci_kernel_f32_n2048_p4096.md).
+# 157.65 MB read + 152.22 MB written; profiles/mci_kernel_f32_n2048_p4096.md).
 # None whenever the kernel has changed since the capture.
-ROOFLINE_TRAFFIC_PER_SIGNAL = (157676288 + 152127488) / 3201
+ROOFLINE_TRAFFIC_PER_SIGNAL = (157651456 + 152223488) / 3201
 
 
 def peaks():
@@ -120,6 +120,26 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def bind_host_to_gpu(torch, index: int):
+    """Run this process on the CPU cores local to GPU `index` (from the PCI device's
+    local_cpulist), so that the page-locked host buffers of the end-to-end measurement are
+    placed in the memory next to that GPU.  Returns the core list, or None if unknown."""
+    try:
+        pr = torch.cuda.get_device_properties(index)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        text = open(f"/sys/bus/pci/devices/{bus}/local_cpulist").read().strip()
+        cpus = set()
+        for part in text.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return text
+    except (OSError, ValueError, AttributeError):
+        return None
+    return None
 
 
 def dist_setup(n_gpus: int, backend: str = "nccl"):
@@ -495,6 +515,7 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    host_cpus = bind_host_to_gpu(torch, local)
     batch = make_batch(rank)
     n_cls = len(P_CHOICES)
     T = [S_FACTOR * p for p in P_CHOICES]
@@ -724,7 +745,7 @@ def main():
             "complex_1d": cplx,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * batch["n_in"] + n_chunks * plan32_stage_bytes,
-                    "chunks": n_chunks,
+                    "chunks": n_chunks, "host_cpus": host_cpus,
                     "d2h_bytes_per_step": 4 * batch["n_out"]},
             "cpu_baseline": cpu,
             "plan": {"smem_bytes": info["smem_bytes"], "signals_per_cta": info["signals_per_cta"][:n_cls]},
