@@ -241,6 +241,38 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def uneven_2d_section(mci, torch, dev, timed, steps):
+    """256 images, LR side ~ U{128..1024}, s ~ U{2,3,4}, M = 2 {f, FD f'}."""
+    from paper_1802_10291_gb300 import synth
+    sysd = [("identity",), ("deriv", 1)]
+    out = {}
+    # --- 256 images, LR side ~ U{128..1024}, s ~ U{2,3,4}
+    rng = synth.rng_for(3, 0)
+    sides = [128, 256, 384, 512, 768, 1024]
+    scales = [2, 3, 4]
+    side = rng.choice(sides, 256)
+    sc = rng.choice(scales, 256)
+    pool = {L: [synth.synthetic_image(rng, L).astype(np.float32) for _ in range(4)] for L in sides}
+    imgs = [pool[int(L)][i % 4] for i, L in enumerate(side)]
+    PT = sorted({(int(L), int(L) * int(k)) for L in sides for k in scales})
+    inter = int(sum(int(L) * int(k) * int(L) for L, k in zip(side, sc)))
+    plan = mci.Plan(sysd, [p for p, _ in PT], [t for _, t in PT], channels="fd", max_batch=1,
+                    max_images=256, max_intermediate=inter)
+    lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), device=dev)
+    n_hr = int(sum(int(k) * int(k) * int(L) * int(L) for L, k in zip(side, sc)))
+    hr = torch.empty(n_hr, device=dev)
+    hh = np.ascontiguousarray(side, np.int32)
+    ss = np.ascontiguousarray(sc, np.int32)
+    n = max(5, steps // 10)
+    t, _ = timed(lambda: plan.upsample_2d(lr, hh, hh, ss, hr, 256), n, 3)
+    ms = 1e3 * t / n
+    out["uneven_256_images"] = {"hr_mpixel_s": n_hr / (ms / 1e3) / 1e6, "ms_per_batch": ms,
+                                "hr_pixels": n_hr, "gbs_lr_plus_hr": 4 * (lr.numel() + n_hr) / (ms / 1e3) / 1e9,
+                                "note": "LR images generated at LR size from a pool of 4 per side"}
+    plan.close()
+    return out
+
+
 def images_2d_section(mci, torch, dev, timed, steps):
     """Image workloads: SISR of 64 synthetic 512^2 images from x2 and x4 decimations, and an
     uneven batch of 256 images (LR side in {128..1024}, scale in {2,3,4})."""
@@ -303,30 +335,7 @@ def images_2d_section(mci, torch, dev, timed, steps):
             "ms_per_batch": ms, "psnr_db_mean": float(np.mean(10 * np.log10(1.0 / mse))),
             "err_vs_oracle_image0": err}
         plan.close()
-    # --- 256 images, LR side ~ U{128..1024}, s ~ U{2,3,4}
-    rng = synth.rng_for(3, 0)
-    sides = [128, 256, 384, 512, 768, 1024]
-    scales = [2, 3, 4]
-    side = rng.choice(sides, 256)
-    sc = rng.choice(scales, 256)
-    pool = {L: [synth.synthetic_image(rng, L).astype(np.float32) for _ in range(4)] for L in sides}
-    imgs = [pool[int(L)][i % 4] for i, L in enumerate(side)]
-    PT = sorted({(int(L), int(L) * int(k)) for L in sides for k in scales})
-    inter = int(sum(int(L) * int(k) * int(L) for L, k in zip(side, sc)))
-    plan = mci.Plan(sysd, [p for p, _ in PT], [t for _, t in PT], channels="fd", max_batch=1,
-                    max_images=256, max_intermediate=inter)
-    lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), device=dev)
-    n_hr = int(sum(int(k) * int(k) * int(L) * int(L) for L, k in zip(side, sc)))
-    hr = torch.empty(n_hr, device=dev)
-    hh = np.ascontiguousarray(side, np.int32)
-    ss = np.ascontiguousarray(sc, np.int32)
-    n = max(5, steps // 10)
-    t, _ = timed(lambda: plan.upsample_2d(lr, hh, hh, ss, hr, 256), n, 3)
-    ms = 1e3 * t / n
-    out["uneven_256_images"] = {"hr_mpixel_s": n_hr / (ms / 1e3) / 1e6, "ms_per_batch": ms,
-                                "hr_pixels": n_hr, "gbs_lr_plus_hr": 4 * (lr.numel() + n_hr) / (ms / 1e3) / 1e9,
-                                "note": "LR images generated at LR size from a pool of 4 per side"}
-    plan.close()
+    out.update(uneven_2d_section(mci, torch, dev, timed, steps))
     return out
 
 
@@ -498,7 +507,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=20000,
                     help="corrector_train case: training pairs (batches of 4, one step each)")
     ap.add_argument("--case", default=None,
-                    choices=["kernel4096", "corrector", "corrector_train", "corrector_small", "sisr_s4"],
+                    choices=["kernel4096", "corrector", "corrector_train", "corrector_small", "sisr_s4",
+                             "uneven2d"],
                     help="profiling case: the P=4096 size-class kernel alone on 3277 signals")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -578,6 +588,11 @@ def main():
         tt, _ = timed(lambda: net.train_step(x, hr, 4, 512, 512, 1e-3), args.steps, args.warmup)
         print(json.dumps({"case": args.case, "forward_ms": 1e3 * tf / args.steps,
                           "train_step_ms": 1e3 * tt / args.steps}), flush=True)
+        return
+    if args.case == "uneven2d":
+        # profiling case: the uneven batch of 256 images (LR side in {128..1024}, s in {2,3,4})
+        out = uneven_2d_section(mci, torch, dev, timed, args.steps)
+        print(json.dumps({"case": args.case, **out}), flush=True)
         return
     if args.case == "sisr_s4":
         # profiling case: 64 synthetic 512^2 images from x4 decimation (tensor-core path)
