@@ -43,6 +43,12 @@ def test_error_strings(mci_lib):
           outputs=("f", "hilbert")), mci.MCI_ERR_INVALID_ARG),
     (dict(systems=[("identity",)], P=16, T=64, max_images=2, max_intermediate=100,
           precision="fp64"), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",), ("deriv", 1)], P=16, T=64, channels="fd", complex_signal=True),
+     mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=64, max_images=2, max_intermediate=100, complex_signal=True),
+     mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=8192, T=8192, complex_signal=True), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[("identity",)], P=10, T=20, complex_signal=True), mci.MCI_ERR_UNSUPPORTED_SIZE),
 ])
 def test_plan_validation(mci_lib, kw, status):
     kw.setdefault("max_batch", 4)
@@ -50,6 +56,11 @@ def test_plan_validation(mci_lib, kw, status):
     h = ctypes.c_void_p()
     assert mci_lib.mci_plan(ctypes.byref(h), ctypes.byref(d), None) == status
     assert h.value is None
+
+
+def test_host_buffer_and_error_entry_points_check_arguments(mci_lib):
+    assert mci_lib.mci_interp_1d_host(None, None, None, None, 1, None) == mci.MCI_ERR_INVALID_ARG
+    assert mci_lib.mci_averaged_error(None, 0, None, 10, 1, None, None, None) == mci.MCI_ERR_INVALID_ARG
 
 
 def test_null_arguments(mci_lib):
