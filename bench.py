@@ -664,11 +664,14 @@ def main():
     k_achieved = k_bytes / (k_ms / 1e3) / 1e9
 
     # ---- image workloads (2-D)
-    images = images_2d_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
-    corr = corrector_section(torch, dev, timed_local) if rank == 0 and not args.no_corrector else None
-    averr = averaged_error_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
-    exact = exactness_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
-    cplx = complex_section(mci, torch, dev, timed_local, args.steps) if rank == 0 else None
+    # single-GPU characterisations of the other workloads: at N = 1 only (under torchrun the
+    # other ranks would idle while rank 0 runs them)
+    solo = rank == 0 and world == 1
+    images = images_2d_section(mci, torch, dev, timed_local, args.steps) if solo else None
+    corr = corrector_section(torch, dev, timed_local) if solo and not args.no_corrector else None
+    averr = averaged_error_section(mci, torch, dev, timed_local, args.steps) if solo else None
+    exact = exactness_section(mci, torch, dev, timed_local, args.steps) if solo else None
+    cplx = complex_section(mci, torch, dev, timed_local, args.steps) if solo else None
 
     # ---- FP64 on the same batch
     plan64, x64, y64, _ = setup("fp64")
@@ -700,7 +703,7 @@ def main():
     # ---- realised error against the FP64 oracle (stratified sample) and the CPU baseline
     cpu = None
     err = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle is timed at N = 1 only
         idx = oracle_sample(batch, n_per_class=CPU_PER_CLASS)
         ref, cpu_s = run_oracle(batch, idx)
         yh = y32.cpu().double().numpy()
