@@ -22,6 +22,11 @@ Functions and the passage each follows:
   Section 3 directly (minimum-norm least squares).
 * :func:`fd_channels` -- the three-point centred differences of Section 5.2.
 * :func:`upsample_2d` -- rows then columns, Section 5.2.
+* :func:`blur_factor`, :func:`blur_systems` -- the blur-aware channel model that
+  Section 5.2 lists as an open extension: every channel is the system response
+  blurred by a periodic Gaussian on the output grid, so each b_m(n) carries the
+  blur's multiplier beta(n); optionally Wiener-regularised (a reading: the paper
+  gives no formula).
 * :func:`averaged_error` -- Eq. (averageerror), Theorem (error).
 * :func:`truth_from_coeffs` -- evaluates a trigonometric polynomial and its
   Hilbert transform from coefficients, Eq. (bandsignal) and Section 2.
@@ -326,16 +331,51 @@ def fd_channels(x, systems):
     return np.stack(chans, axis=-2)
 
 
-def upsample_2d(img, scale, systems, policy="pinv", nthreads=0):
+def blur_factor(n, T, taps, sigma):
+    """Multiplier beta(n) = sum_{k=-K..K} w_k e^{-2 pi i n k / T} of the circular convolution
+    y(t) = sum_k w_k x(t - 2 pi k / T) on the T-point output grid, where w is the normalised
+    Gaussian w_k = exp(-k^2 / (2 sigma^2)) / sum_j exp(-j^2 / (2 sigma^2)), K = taps // 2."""
+    K = taps // 2
+    k = np.arange(-K, K + 1, dtype=np.float64)
+    w = np.exp(-k * k / (2.0 * sigma * sigma))
+    w /= w.sum()
+    n = np.asarray(n, np.float64)
+    return np.exp(-2j * np.pi * np.multiply.outer(n, k) / T) @ w
+
+
+def blur_systems(systems, P, T, taps, sigma, lam=0.0, N1=None):
+    """Blur-aware channel model: custom systems b_m(n) gamma(n) over the band.
+    lam = 0: gamma = beta, i.e. every measured channel is the blurred system response, and MCI
+    then recovers the unblurred signal where the blurred band is recoverable.
+    lam > 0 (Wiener-type regularisation, normalised to 1 at n = 0):
+    gamma = (|beta|^2 + lam) / ((1 + lam) conj beta), i.e. the reconstruction of the plain
+    channel model multiplied by (1 + lam) conj beta / (|beta|^2 + lam)."""
+    M = len(systems)
+    N1 = default_n1(M, P) if N1 is None else N1
+    band = np.arange(N1, N1 + M * P, dtype=np.int64)
+    beta = blur_factor(band, T, taps, sigma)
+    gamma = beta if lam == 0 else (np.abs(beta) ** 2 + lam) / ((1.0 + lam) * np.conj(beta))
+    return [("custom", multiplier(sy, band, P, N1) * gamma) for sy in systems]
+
+
+def upsample_2d(img, scale, systems, policy="pinv", nthreads=0, blur=None):
     """Separable 2-D MCI of Section 5.2: every row (length w) is interpolated to s*w samples
     from its FD-derived channels, then every column (length h) of that result to s*h.
-    Pixel p of a row sits at t_p = 2 pi p / w; output pixel j at 2 pi j / (s w)."""
+    Pixel p of a row sits at t_p = 2 pi p / w; output pixel j at 2 pi j / (s w).
+    blur = (taps, sigma, lam): each pass uses the blur-aware model of :func:`blur_systems`
+    for a taps-tap Gaussian along its axis (the 2-D Gaussian is the outer product)."""
     img = np.asarray(img, np.float64)
     h, w = img.shape
-    rows = mci_direct(systems, fd_channels(img, systems), scale * w, policy=policy,
+
+    def model(P, T):
+        if blur is None:
+            return systems
+        return blur_systems(systems, P, T, blur[0], blur[1], blur[2] if len(blur) > 2 else 0.0)
+
+    rows = mci_direct(model(w, scale * w), fd_channels(img, systems), scale * w, policy=policy,
                       nthreads=nthreads)[:, 0, :]                      # h x sw
-    cols = mci_direct(systems, fd_channels(rows.T, systems), scale * h, policy=policy,
-                      nthreads=nthreads)[:, 0, :]                      # sw x sh
+    cols = mci_direct(model(h, scale * h), fd_channels(rows.T, systems), scale * h,
+                      policy=policy, nthreads=nthreads)[:, 0, :]       # sw x sh
     return cols.T
 
 

@@ -237,6 +237,38 @@ def decimate(img, s):
     return np.ascontiguousarray(np.asarray(img)[..., ::s, ::s])
 
 
+def gaussian_kernel_1d(taps, sigma):
+    """Normalised 1-D Gaussian of ``taps`` (odd) samples at integer offsets -K..K, K = taps // 2:
+    w_k = exp(-k^2 / (2 sigma^2)) / sum_j exp(-j^2 / (2 sigma^2)).  The square taps x taps
+    Gaussian of the paper's degradation (5 x 5, standard deviation 1.0, Section 5.2) is the
+    outer product of two of these."""
+    if taps < 1 or taps % 2 == 0 or not sigma > 0:
+        raise ValueError("taps must be odd and positive, sigma positive")
+    k = np.arange(-(taps // 2), taps // 2 + 1, dtype=np.float64)
+    w = np.exp(-k * k / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def blur_periodic(x, taps, sigma, axes=(-1,)):
+    """Circular convolution of x with the normalised Gaussian along each of ``axes``
+    (periodic images, as MCI assumes): y[i] = sum_k w_k x[i - k], indices wrapped."""
+    w = gaussian_kernel_1d(taps, sigma)
+    K = taps // 2
+    y = np.asarray(x, np.float64)
+    for ax in axes:
+        acc = np.zeros_like(y)
+        for j, wk in enumerate(w):
+            acc += wk * np.roll(y, j - K, axis=ax)
+        y = acc
+    return y
+
+
+def degrade(img, s, taps=5, sigma=1.0):
+    """The degradation of the paper's super-resolution experiment (Section 5.2): blur by a
+    taps x taps Gaussian (periodic boundary), then keep every s-th pixel (offset 0)."""
+    return decimate(blur_periodic(img, taps, sigma, axes=(-2, -1)), s)
+
+
 def image_params(rng, n, size):
     """Parameters of n synthetic size x size images for the device generator (192 floats per
     image): 20 blobs (cy, cx, 1/s_major, 1/s_minor, angle, amp) with s_major ~ U(size/64, size/8),
