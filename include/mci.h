@@ -138,6 +138,23 @@ typedef struct {
                                 from 6 to 3072, and one signal's max(M, s * n_out) buffers of
                                 P complex values must fit in shared memory (else
                                 MCI_ERR_UNSUPPORTED_SIZE; e.g. FP64 M = 3, s = 2, P = 4096). */
+    int blur_taps;           /* 0: no blur.  Otherwise an odd tap count, 1 .. 255: the blur-aware
+                                channel model that Section 5.2 leaves as an open extension.
+                                Every channel is taken to be its system's response circularly
+                                convolved, before sampling, with the normalised Gaussian
+                                w_k = exp(-k^2 / (2 blur_sigma^2)) / sum_j (same), |k| <= taps/2,
+                                on the output grid (spacing 2 pi / T of the size class; in 2-D
+                                along each axis, i.e. the separable taps x taps Gaussian of the
+                                paper's degradation).  Its multiplier beta(n) = sum_k w_k
+                                e^{-2 pi i n k / T} then multiplies every b_m(n).            */
+    double blur_sigma;       /* standard deviation in output samples, > 0 when blur_taps > 0  */
+    double blur_lambda;      /* >= 0.  0: exact model, the unblurred model's reconstruction
+                                divided by beta(n) (where |beta(n)| < singular_rtol the factor
+                                follows singular_policy: 0 for PINV and ZERO, MCI_ERR_SINGULAR
+                                for ERROR; such frequencies add to n_singular).  > 0: Wiener-
+                                type regularisation, the unblurred model's reconstruction times
+                                (1 + lambda) conj beta(n) / (|beta(n)|^2 + lambda), which is 1
+                                at n = 0.  Plans with a blur take no mci_averaged_error.    */
 } mci_desc;
 
 typedef struct {

@@ -77,8 +77,17 @@ mci_status mci_corrector_destroy(mci_corrector_t net);
 mci_status mci_generate_images(const float* params, float* img, int n, int h, int w,
                                mci_stream_t stream);
 
-/* Pure decimation lr[y][x] = hr[s y][s x] of n images h x w (h, w multiples of s). */
+/* Pure decimation lr[y][x] = hr[s y][s x] of n images h x w (h, w multiples of s;
+ * 1 <= n <= 65535). */
 mci_status mci_decimate(const float* hr, float* lr, int n, int h, int w, int s, mci_stream_t stream);
+
+/* The degradation of the paper's super-resolution experiment (Section 5.2): blur by the
+ * taps x taps Gaussian of standard deviation sigma (pixels; normalised outer product of
+ * w_k = exp(-k^2 / (2 sigma^2)), |k| <= taps / 2; periodic boundary), then decimate by s:
+ * lr[y][x] = sum_{i,j} w_i w_j hr[(s y - i) mod h][(s x - j) mod w].  taps odd, 1 .. 255,
+ * sigma > 0; otherwise as mci_decimate.  FP32 accumulation. */
+mci_status mci_degrade(const float* hr, float* lr, int n, int h, int w, int s, int taps, double sigma,
+                       mci_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -32,9 +32,12 @@ def _lib():
         lib.mci_corrector_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         lib.mci_generate_images.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
         lib.mci_decimate.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+        lib.mci_degrade.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double, vp]
         for f in ("mci_corrector_create", "mci_corrector_forward", "mci_corrector_loss_grad",
                   "mci_corrector_train_step", "mci_corrector_get_state", "mci_corrector_set_state",
-                  "mci_corrector_destroy", "mci_corrector_status", "mci_generate_images", "mci_decimate"):
+                  "mci_corrector_destroy", "mci_corrector_status", "mci_generate_images", "mci_decimate",
+                  "mci_degrade"):
             getattr(lib, f).restype = ctypes.c_int
         _bound = True
     return lib
@@ -149,6 +152,12 @@ def generate_images(params_dev, img_dev, n, h, w, stream=None):
 def decimate(hr_dev, lr_dev, n, h, w, s, stream=None):
     mci._check(_lib().mci_decimate(mci._ptr(hr_dev), mci._ptr(lr_dev), n, h, w, s, _stream(stream)),
                "mci_decimate")
+
+
+def degrade(hr_dev, lr_dev, n, h, w, s, taps=5, sigma=1.0, stream=None):
+    """Gaussian blur (taps x taps, periodic) then decimation by s, on the device."""
+    mci._check(_lib().mci_degrade(mci._ptr(hr_dev), mci._ptr(lr_dev), n, h, w, s, int(taps),
+                                  float(sigma), _stream(stream)), "mci_degrade")
 
 
 class PairSource:

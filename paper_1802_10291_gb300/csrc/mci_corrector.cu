@@ -596,6 +596,37 @@ __global__ void decimate_kernel(const float* __restrict__ hr, float* __restrict_
     lr[((int64_t)b * h + y) * w + x] = hr[((int64_t)b * H + (int64_t)s * y) * W + (int64_t)s * x];
 }
 
+// Gaussian blur (periodic) followed by decimation: lr[y][x] = sum_{i,j} w_i w_j
+// hr[(s y - i) mod H][(s x - j) mod W], |i|, |j| <= K; one thread per LR pixel.
+struct BlurTaps {
+    float w[256];
+    int K;
+};
+
+__device__ __forceinline__ int wrap_index(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+__global__ void degrade_kernel(const float* __restrict__ hr, float* __restrict__ lr, int H, int W, int s,
+                               const BlurTaps t)
+{
+    const int b = blockIdx.z;
+    const int h = H / s, w = W / s;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= h || x >= w) return;
+    const float* img = hr + (int64_t)b * H * W;
+    float acc = 0.f;
+    for (int i = -t.K; i <= t.K; ++i) {
+        const float* row = img + (int64_t)wrap_index(s * y - i, H) * W;
+        float r = 0.f;
+        for (int j = -t.K; j <= t.K; ++j) r = fmaf(t.w[j + t.K], __ldg(row + wrap_index(s * x - j, W)), r);
+        acc = fmaf(t.w[i + t.K], r, acc);
+    }
+    lr[((int64_t)b * h + y) * w + x] = acc;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -881,9 +912,27 @@ mci_status mci_generate_images(const float* params, float* img, int n, int h, in
 
 mci_status mci_decimate(const float* hr, float* lr, int n, int h, int w, int s, mci_stream_t stream)
 {
-    if (!hr || !lr || n <= 0 || s <= 0 || h % s || w % s) return MCI_ERR_INVALID_ARG;
+    if (!hr || !lr || n <= 0 || n > 65535 || s <= 0 || h <= 0 || w <= 0 || h % s || w % s)
+        return MCI_ERR_INVALID_ARG;
     const dim3 blk(32, 8), grid((w / s + 31) / 32, (h / s + 7) / 8, n);
     decimate_kernel<<<grid, blk, 0, (cudaStream_t)stream>>>(hr, lr, h, w, s);
+    return cudaGetLastError() == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+mci_status mci_degrade(const float* hr, float* lr, int n, int h, int w, int s, int taps, double sigma,
+                       mci_stream_t stream)
+{
+    if (!hr || !lr || n <= 0 || n > 65535 || s <= 0 || h <= 0 || w <= 0 || h % s || w % s)
+        return MCI_ERR_INVALID_ARG;
+    if (taps < 1 || taps > 255 || taps % 2 == 0 || !(sigma > 0.0) || !std::isfinite(sigma))
+        return MCI_ERR_INVALID_ARG;
+    BlurTaps t{};
+    t.K = taps / 2;
+    double sum = 0.0, wd[256];
+    for (int k = -t.K; k <= t.K; ++k) sum += (wd[k + t.K] = std::exp(-(double)k * k / (2.0 * sigma * sigma)));
+    for (int k = 0; k < taps; ++k) t.w[k] = (float)(wd[k] / sum);
+    const dim3 blk(32, 8), grid((w / s + 31) / 32, (h / s + 7) / 8, n);
+    degrade_kernel<<<grid, blk, 0, (cudaStream_t)stream>>>(hr, lr, h, w, s, t);
     return cudaGetLastError() == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
 }
 

@@ -58,6 +58,37 @@ cd output_multiplier(int op, int64_t n)
     return 1.0;
 }
 
+// Blur-aware channel model (the extension Section 5.2 leaves open): each channel is
+// blurred before sampling by the normalised Gaussian w_k, |k| <= K, on the T-grid, whose
+// multiplier is beta(n) = sum_k w_k e^{-2 pi i n k / T}.  Returns the factor the unblurred
+// model's reconstruction is multiplied by at frequency n: 1 / beta(n) (lambda = 0) or
+// (1 + lambda) conj beta / (|beta|^2 + lambda); *singular set where lambda = 0 and
+// |beta(n)| < rtol (the factor is then 0).
+cd blur_output_factor(const mci_desc& d, const std::vector<double>& w, int T, int64_t n, double rtol,
+                      bool* singular)
+{
+    const int K = d.blur_taps / 2;
+    cd beta = 0.0;
+    for (int k = -K; k <= K; ++k) beta += w[k + K] * cis_frac(-n * (int64_t)k, T);
+    *singular = false;
+    if (d.blur_lambda > 0.0) return (1.0 + d.blur_lambda) * std::conj(beta) / (std::norm(beta) + d.blur_lambda);
+    if (std::abs(beta) < rtol) {
+        *singular = true;
+        return 0.0;
+    }
+    return 1.0 / beta;
+}
+
+std::vector<double> blur_taps_of(const mci_desc& d)
+{
+    const int K = d.blur_taps / 2;
+    std::vector<double> w(2 * K + 1);
+    double sum = 0.0;
+    for (int k = -K; k <= K; ++k) sum += (w[k + K] = std::exp(-(double)k * k / (2.0 * d.blur_sigma * d.blur_sigma)));
+    for (double& v : w) v /= sum;
+    return w;
+}
+
 // One-sided (Hestenes) Jacobi SVD of an M x M complex matrix, row-major:
 // on return A holds U * diag(sigma) column-wise, V the right singular vectors.
 void jacobi_svd(int M, std::vector<cd>& A, std::vector<cd>& V)
@@ -296,6 +327,11 @@ mci_status validate(const mci_desc* d)
                 return MCI_ERR_INVALID_ARG;
         }
     }
+    if (d->blur_taps < 0 || d->blur_taps > 255 || (d->blur_taps > 0 && d->blur_taps % 2 == 0))
+        return MCI_ERR_INVALID_ARG;
+    if (d->blur_taps > 0 && !(d->blur_sigma > 0.0 && std::isfinite(d->blur_sigma) &&
+                              d->blur_lambda >= 0.0 && std::isfinite(d->blur_lambda)))
+        return MCI_ERR_INVALID_ARG;
     if (d->complex_signal != 0 && d->complex_signal != 1) return MCI_ERR_INVALID_ARG;
     if (d->complex_signal && (d->channel_mode != MCI_CHANNELS_MEASURED || d->max_images > 0))
         return MCI_ERR_INVALID_ARG;
@@ -393,16 +429,31 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
             osum += om;
         }
         p->omega_sum[c] = osum;
+        std::vector<cd> omega;   // blur factor over the band, n = N1 .. N1 + M P - 1
+        if (d.blur_taps > 0) {
+            const std::vector<double> w = blur_taps_of(d);
+            omega.resize((size_t)M * P);
+            for (int64_t i = 0; i < (int64_t)M * P; ++i) {
+                bool sing = false;
+                omega[i] = blur_output_factor(d, w, T, hc.N1 + i, rtol, &sing);
+                if (sing) {
+                    ++p->n_singular;
+                    if (d.singular_policy == MCI_SINGULAR_ERROR) return MCI_ERR_SINGULAR;
+                }
+            }
+        }
         ClassDev& cd_ = p->cdev[c];
         if ((W.size() / 2) % 2) push_cpx(W, cd(0.0));  // 16-byte aligned class region
         cd_.w_off = (int64_t)(W.size() / 2);
-        // W_r[m][q] = (1/P) sum_j Q_r[m][j] o(n_j) e^{2 pi i n_j u / T}, n_j = N1 + r + j P
+        // W_r[m][q] = (1/P) sum_j Q_r[m][j] o(n_j) omega(n_j) e^{2 pi i n_j u / T},
+        // n_j = N1 + r + j P (omega = 1 without a blur)
         auto Wfull = [&](int r, int m, int q) {
             const int o = ops[q / s], u = q % s;
             cd acc = 0.0;
             for (int j = 0; j < M; ++j) {
                 const int64_t n = hc.N1 + r + (int64_t)j * P;
-                acc += inv.Q[((size_t)r * M + m) * M + j] * output_multiplier(o, n) *
+                const cd om = omega.empty() ? cd(1.0) : omega[(size_t)(r + (int64_t)j * P)];
+                acc += inv.Q[((size_t)r * M + m) * M + j] * output_multiplier(o, n) * om *
                        cis_frac(n * (int64_t)u, T);
             }
             return acc / (double)P;
@@ -1190,6 +1241,7 @@ mci_status mci_averaged_error(mci_plan_t p, int size_class, const double* coeffs
     if (d.channel_mode != MCI_CHANNELS_MEASURED) return MCI_ERR_INVALID_ARG;
     for (int m = 0; m < d.M; ++m)
         if (d.sys[m].kind == MCI_SYS_CUSTOM) return MCI_ERR_INVALID_ARG;   // b(n) known only in the band
+    if (d.blur_taps > 0) return MCI_ERR_INVALID_ARG;   // the error kernel has no blur factor
     const HostClass& hc = p->cls[size_class];
     const int64_t mu = (int64_t)d.M * hc.P;
     if (n_max < std::max<int64_t>(-hc.N1, hc.N1 + mu - 1)) return MCI_ERR_INVALID_ARG;   // band inside

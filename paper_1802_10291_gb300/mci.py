@@ -61,7 +61,8 @@ class mci_desc(ctypes.Structure):
                 ("singular_rtol", ctypes.c_double), ("channel_mode", ctypes.c_int),
                 ("max_batch", ctypes.c_int64), ("max_images", ctypes.c_int64),
                 ("max_intermediate", ctypes.c_int64), ("autotune", ctypes.c_int),
-                ("complex_signal", ctypes.c_int)]
+                ("complex_signal", ctypes.c_int), ("blur_taps", ctypes.c_int),
+                ("blur_sigma", ctypes.c_double), ("blur_lambda", ctypes.c_double)]
 
 
 class mci_plan_stats(ctypes.Structure):
@@ -160,10 +161,11 @@ def _stream(stream):
 
 def make_desc(systems, P, T, N1=None, outputs=("f",), precision="fp32", singular="pinv",
               singular_rtol=0.0, channels="measured", max_batch=1, max_images=0,
-              max_intermediate=0, autotune=False, complex_signal=False):
+              max_intermediate=0, autotune=False, complex_signal=False, blur=None):
     """Build an mci_desc (plus the arrays it points to, kept alive on the returned object).
     systems: list of ('identity',), ('deriv', k), ('hilbert',), ('shift', tau), ('custom', table)
-    where table is a float64 array of 2*M*P_c values per size class, concatenated."""
+    where table is a float64 array of 2*M*P_c values per size class, concatenated.
+    blur: None, or (taps, sigma[, lambda]) for the blur-aware channel model."""
     P = [int(p) for p in (P if hasattr(P, "__len__") else [P])]
     T = [int(t) for t in (T if hasattr(T, "__len__") else [T])]
     sysarr = (mci_system * len(systems))()
@@ -201,6 +203,10 @@ def make_desc(systems, P, T, N1=None, outputs=("f",), precision="fp32", singular
     d.max_intermediate = int(max_intermediate)
     d.autotune = 1 if autotune else 0
     d.complex_signal = 1 if complex_signal else 0
+    if blur is not None:
+        d.blur_taps = int(blur[0])
+        d.blur_sigma = float(blur[1])
+        d.blur_lambda = float(blur[2]) if len(blur) > 2 else 0.0
     d._keep = (sysarr, Parr, Tarr, N1arr, keep)
     return d
 

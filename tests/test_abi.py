@@ -16,7 +16,7 @@ def test_exports_every_declared_symbol(mci_lib):
                              "mci_corrector_num_params", "mci_corrector_create", "mci_corrector_forward",
                              "mci_corrector_loss_grad", "mci_corrector_train_step",
                              "mci_corrector_get_state", "mci_corrector_set_state", "mci_corrector_status",
-                             "mci_corrector_destroy", "mci_generate_images", "mci_decimate"}
+                             "mci_corrector_destroy", "mci_generate_images", "mci_decimate", "mci_degrade"}
     for name in declared:
         assert hasattr(mci_lib, name), name
 
@@ -49,6 +49,12 @@ def test_error_strings(mci_lib):
      mci.MCI_ERR_INVALID_ARG),
     (dict(systems=[("identity",)], P=8192, T=8192, complex_signal=True), mci.MCI_ERR_UNSUPPORTED_SIZE),
     (dict(systems=[("identity",)], P=10, T=20, complex_signal=True), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[("identity",)], P=16, T=48, blur=(4, 1.0)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=48, blur=(5, 0.0)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=48, blur=(5, 1.0, -0.1)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=48, blur=(257, 1.0)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=48, blur=(-1, 1.0)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[("identity",)], P=16, T=48, blur=(5, float("nan"))), mci.MCI_ERR_INVALID_ARG),
 ])
 def test_plan_validation(mci_lib, kw, status):
     kw.setdefault("max_batch", 4)
@@ -82,6 +88,11 @@ def test_corrector_host_checks(mci_lib):
     assert mci_lib.mci_corrector_forward(None, None, None, 1, 8, 8, None) == mci.MCI_ERR_INVALID_ARG
     assert mci_lib.mci_corrector_destroy(None) == mci.MCI_OK
     assert mci_lib.mci_decimate(None, None, 1, 8, 8, 3, None) == mci.MCI_ERR_INVALID_ARG
+    lib = corrector._lib()
+    assert lib.mci_degrade(None, None, 1, 9, 9, 3, 5, 1.0, None) == mci.MCI_ERR_INVALID_ARG
+    assert lib.mci_degrade(1 << 20, 1 << 21, 1, 9, 9, 3, 4, 1.0, None) == mci.MCI_ERR_INVALID_ARG
+    assert lib.mci_degrade(1 << 20, 1 << 21, 1, 9, 9, 3, 5, -1.0, None) == mci.MCI_ERR_INVALID_ARG
+    assert lib.mci_degrade(1 << 20, 1 << 21, 1, 8, 9, 3, 5, 1.0, None) == mci.MCI_ERR_INVALID_ARG
     assert mci_lib.mci_generate_images(None, None, 1, 8, 8, None) == mci.MCI_ERR_INVALID_ARG
 
 
