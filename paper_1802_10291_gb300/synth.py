@@ -90,6 +90,76 @@ def channel_samples(coeffs, freqs, systems, P):
     return np.stack(chans, axis=-2)
 
 
+def response_2d(system, ny, nx):
+    """Fourier multiplier of a 2-D linear system at integer frequencies (ny, nx) (rows y,
+    columns x): identity 1; partial derivative ('partial', a, b) (i ny)^a (i nx)^b;
+    Laplacian -(ny^2 + nx^2); shift ('shift', ty, tx) e^{i (ny ty + nx tx)}; Riesz transform
+    ('riesz', axis) -i n_axis / |n| (0 at n = 0), axis 0 = y, 1 = x."""
+    ny = np.asarray(ny, np.float64)
+    nx = np.asarray(nx, np.float64)
+    ny, nx = np.broadcast_arrays(ny, nx)
+    kind = system[0]
+    if kind == "identity":
+        return np.ones(ny.shape, np.complex128)
+    if kind == "partial":
+        return (1j * ny) ** int(system[1]) * (1j * nx) ** int(system[2])
+    if kind == "laplacian":
+        return -(ny * ny + nx * nx) + 0j
+    if kind == "shift":
+        return np.exp(1j * (ny * float(system[1]) + nx * float(system[2])))
+    if kind == "riesz":
+        r = np.hypot(ny, nx)
+        n_ax = ny if int(system[1]) == 0 else nx
+        return np.where(r > 0, -1j * n_ax / np.where(r > 0, r, 1.0), 0.0)
+    raise ValueError(kind)
+
+
+def sample_coeffs_2d(coeffs, band_y, band_x, shape):
+    """Exact values of sum_n c(n) e^{i (ny t1 + nx t2)} on the grid t = (2 pi l1 / T1,
+    2 pi l2 / T2), l < shape = (T1, T2); coeffs [..., len(band_y), len(band_x)].
+    Frequencies are folded modulo the grid (exact aliasing) before one inverse FFT."""
+    T1, T2 = shape
+    coeffs = np.asarray(coeffs, np.complex128)
+    lead = coeffs.shape[:-2]
+    bins = np.zeros(lead + (T1, T2), np.complex128)
+    iy = np.mod(np.asarray(band_y, np.int64), T1)
+    ix = np.mod(np.asarray(band_x, np.int64), T2)
+    for a, ya in enumerate(iy):
+        np.add.at(bins[..., ya, :], (Ellipsis, ix), coeffs[..., a, :])
+    return np.fft.ifft2(bins, axes=(-2, -1)) * (T1 * T2)
+
+
+def channel_samples_2d(coeffs, band_y, band_x, systems, P):
+    """Real samples of every 2-D system's response on the P = (P1, P2) grid: [..., M, P1, P2]."""
+    ny, nx = np.meshgrid(band_y, band_x, indexing="ij")
+    return np.stack([sample_coeffs_2d(np.asarray(coeffs) * response_2d(s, ny, nx), band_y, band_x, P).real
+                     for s in systems], axis=-3)
+
+
+def trig_poly_2d(rng, band_y, band_x, batch=None):
+    """Real 2-D trigonometric polynomial over band_y x band_x: for each pair n, -n both in the
+    band, Re and Im of a(n) ~ N(0,1) / (1 + |ny| + |nx|) with a(-n) = conj a(n); a(0) ~ N(0,1);
+    frequencies whose mirror image is outside the band get 0."""
+    by, bx = np.asarray(band_y, np.int64), np.asarray(band_x, np.int64)
+    lead = () if batch is None else (batch,)
+    a = np.zeros(lead + (by.size, bx.size), np.complex128)
+    iy = {int(v): i for i, v in enumerate(by)}
+    ix = {int(v): i for i, v in enumerate(bx)}
+    for y in by:
+        for x in bx:
+            y, x = int(y), int(x)
+            if -y not in iy or -x not in ix or (y, x) < (-y, -x):
+                continue
+            scale = 1.0 / (1.0 + abs(y) + abs(x))
+            if (y, x) == (0, 0):
+                a[..., iy[0], ix[0]] = rng.standard_normal(lead)
+                continue
+            z = (rng.standard_normal(lead) + 1j * rng.standard_normal(lead)) * scale
+            a[..., iy[y], ix[x]] = z
+            a[..., iy[-y], ix[-x]] = np.conj(z)
+    return a
+
+
 # ---------------------------------------------------------------------------
 # signals
 # ---------------------------------------------------------------------------
