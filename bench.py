@@ -387,6 +387,38 @@ def complex_section(mci, torch, dev, timed, steps):
             "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm, "fp32_err_over_rms_2_signals": err}
 
 
+def mci2d_section(torch, dev, timed, steps):
+    """Two-dimensional MCI (the 2-D method of the open directions of Section 5.2): 64 images,
+    channels {f, f_x, f_y, f_xy} on a 2 x 2 alias lattice, 256 x 256 samples per channel, output
+    768 x 768 (x3 per axis), FP32; bandlimited synthetic inputs (4 distinct images, repeated) so
+    that the realised error against the exact image is known.  Inputs plus outputs (218 MB per
+    batch) are larger than L2."""
+    from paper_1802_10291_gb300 import mci2d, synth
+    from oracle import mci2d as o2
+    systems = [("identity",), ("partial", 0, 1), ("partial", 1, 0), ("partial", 1, 1)]
+    grid, P, T, n_img = (2, 2), (256, 256), (768, 768), 64
+    by, bx = o2.band(grid, P)
+    a = synth.trig_poly_2d(synth.rng_for(16), by, bx, 4)
+    g = synth.channel_samples_2d(a, by, bx, systems, P).astype(np.float32)
+    x = torch.tensor(np.concatenate([g] * (n_img // 4)), device=dev)
+    y = torch.empty((n_img,) + T, device=dev)
+    plan = mci2d.Plan2D(systems, grid, P, T, max_batch=n_img)
+    n = max(10, steps // 10)
+    t, _ = timed(lambda: plan.interp(x, y), n, 3)
+    ms = 1e3 * t / n
+    truth = synth.sample_coeffs_2d(a[0], by, bx, T).real
+    got = y[0].double().cpu().numpy()
+    err = float(np.max(np.abs(got - truth)) / np.sqrt(np.mean(truth ** 2)))
+    byts = (x.numel() + y.numel()) * 4
+    hbm, _ = peaks()
+    info = plan.info()
+    plan.close()
+    return {"images": n_img, "systems": [list(v) for v in systems], "P": list(P), "T": list(T), "ms": ms,
+            "hr_mpixel_s": n_img * T[0] * T[1] / (ms / 1e3) / 1e6, "gbs_in_plus_out": byts / (ms / 1e3) / 1e9,
+            "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm, "workspace_bytes": info["workspace_bytes"],
+            "fp32_err_over_rms_vs_exact": err, "launches_per_call": 3}
+
+
 def exactness_section(mci, torch, dev, timed, steps):
     """One real trig polynomial on the band {-64..63}, M = 2 {f, f'}, P = 64: f and its Hilbert
     transform at T = 4096 in FP64 and FP32 -- latency of one call and the error against the
@@ -529,7 +561,7 @@ def main():
                     help="corrector_train case: training pairs (batches of 4, one step each)")
     ap.add_argument("--case", default=None,
                     choices=["kernel4096", "corrector", "corrector_train", "corrector_small", "sisr_s4",
-                             "uneven2d", "images"],
+                             "uneven2d", "images", "mci2d"],
                     help="profiling case: the P=4096 size-class kernel alone on 3277 signals")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -609,6 +641,10 @@ def main():
         tt, _ = timed(lambda: net.train_step(x, hr, 4, 512, 512, 1e-3), args.steps, args.warmup)
         print(json.dumps({"case": args.case, "forward_ms": 1e3 * tf / args.steps,
                           "train_step_ms": 1e3 * tt / args.steps}), flush=True)
+        return
+    if args.case == "mci2d":
+        # two-dimensional MCI alone (three kernels per call)
+        print(json.dumps({"case": args.case, **mci2d_section(torch, dev, timed, args.steps)}), flush=True)
         return
     if args.case == "images":
         # every image workload: SISR x2/x4, x3 with M = 2 and 3, the blurred x3 set, uneven batch
@@ -698,6 +734,7 @@ def main():
     averr = averaged_error_section(mci, torch, dev, timed_local, args.steps) if solo else None
     exact = exactness_section(mci, torch, dev, timed_local, args.steps) if solo else None
     cplx = complex_section(mci, torch, dev, timed_local, args.steps) if solo else None
+    two_d = mci2d_section(torch, dev, timed_local, args.steps) if solo else None
 
     # ---- FP64 on the same batch
     plan64, x64, y64, _ = setup("fp64")
@@ -787,6 +824,7 @@ def main():
             "averaged_error": averr,
             "exactness_m2_p64": exact,
             "complex_1d": cplx,
+            "mci_2d": two_d,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 4 * batch["n_in"] + n_chunks * plan32_stage_bytes,
                     "chunks": n_chunks, "host_cpus": host_cpus,

@@ -1,0 +1,310 @@
+// Two-dimensional multichannel interpolation (include/mci2d.h): plan construction in
+// FP64 on the host and three kernels.
+//
+//   mci2_rowfwd   forward FFT of every channel row (two real rows per complex FFT),
+//                 half spectrum stored column-major per channel: X[b][m][k2][p1]
+//   mci2_col      per half-spectrum column k2: forward column FFTs of the M channels,
+//                 per-residue solve (Eq. (matrixeqn1) on Z^2) for the M aliases of bin k
+//                 and of bin -k, then for every output phase (u1, u2) the Hermitian-
+//                 symmetrised sub-grid spectrum and its inverse column FFT:
+//                 Z[b][u2][k2][j1], j1 = s1 p1 + u1
+//   mci2_rowinv   per output row j1 and phase u2: inverse real FFT over k2 (two real
+//                 outputs per complex FFT), interleaved into out[b][j1][s2 p2 + u2]
+//
+// The FFTs are shared-memory Stockham transforms of runtime length (radix 4, then 2,
+// then one radix-3 pass), all threads of the CTA working on several sequences.
+#include <cuda_runtime.h>
+
+#include "mci2d_internal.h"
+
+using mci2::Dims2;
+using mci2::kThreads2;
+
+namespace {
+
+template <typename R>
+struct alignas(2 * sizeof(R)) zc {
+    R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ zc<R> zmul(zc<R> a, zc<R> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ zc<R> zadd(zc<R> a, zc<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ zc<R> zsub(zc<R> a, zc<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ zc<R> zconj(zc<R> a) { return {a.re, -a.im}; }
+// a * (+i) when s > 0, a * (-i) when s < 0
+template <typename R>
+__device__ __forceinline__ zc<R> zrot(zc<R> a, bool plus_i) { return plus_i ? zc<R>{-a.im, a.re} : zc<R>{a.im, -a.re}; }
+
+// In-place-free Stockham FFT of `count` sequences of length N stored contiguously (stride N)
+// in a; b is scratch of the same size.  Forward: X_k = sum_p x_p e^{-2 pi i k p / N}; inverse:
+// the conjugate kernel, unnormalised.  roots[k] = e^{-2 pi i k / N}.  Radix 4 while 4 | rem,
+// then 2, then 3, so the stride p before every pass is a power of two.  Returns the buffer
+// holding the result.  All threads of the block must call it.
+template <typename R>
+__device__ zc<R>* fft_seq(zc<R>* a, zc<R>* b, int N, int count, const zc<R>* __restrict__ roots, bool inv)
+{
+    zc<R>* src = a;
+    zc<R>* dst = b;
+    int p = 1, lp = 0, rem = N;
+    while (rem > 1) {
+        const int r = rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : 3);
+        const int nb = N / r;
+        const int step = N / (p * r);
+        const int total = count * nb;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int sq = idx / nb;
+            const int i = idx - sq * nb;
+            const int k = i & (p - 1);
+            const zc<R>* s = src + (size_t)sq * N + i;
+            zc<R>* d = dst + (size_t)sq * N + ((i >> lp) * p * r + k);
+            zc<R> x[4];
+            for (int j = 0; j < r; ++j) {
+                zc<R> v = s[j * nb];
+                if (j > 0 && k > 0) {
+                    zc<R> w = roots[j * k * step];
+                    if (inv) w.im = -w.im;
+                    v = zmul(v, w);
+                }
+                x[j] = v;
+            }
+            if (r == 4) {
+                const zc<R> t0 = zadd(x[0], x[2]), t1 = zsub(x[0], x[2]);
+                const zc<R> t2 = zadd(x[1], x[3]), t3 = zsub(x[1], x[3]);
+                // forward: X1 = t1 - i t3, X3 = t1 + i t3; inverse the other way round
+                const zc<R> it3 = zrot(t3, inv);
+                d[0] = zadd(t0, t2);
+                d[p] = zadd(t1, it3);
+                d[2 * p] = zsub(t0, t2);
+                d[3 * p] = zsub(t1, it3);
+            } else if (r == 2) {
+                d[0] = zadd(x[0], x[1]);
+                d[p] = zsub(x[0], x[1]);
+            } else {
+                const R h = (R)0.86602540378443864676;   // sin(2 pi / 3)
+                const zc<R> t1 = zadd(x[1], x[2]), t2 = zsub(x[1], x[2]);
+                const zc<R> m = {x[0].re - (R)0.5 * t1.re, x[0].im - (R)0.5 * t1.im};
+                const zc<R> it2 = zrot(zc<R>{h * t2.re, h * t2.im}, inv);   // forward: -i h t2
+                d[0] = zadd(x[0], t1);
+                d[p] = zadd(m, it2);
+                d[2 * p] = zsub(m, it2);
+            }
+        }
+        __syncthreads();
+        zc<R>* t = src;
+        src = dst;
+        dst = t;
+        p *= r;
+        lp += (r == 4) ? 2 : (r == 2 ? 1 : 0);
+        rem /= r;
+    }
+    return src;
+}
+
+// -------------------------------------------------------------------------------------------
+// pass 1: row FFTs of every channel plane, two real rows per complex FFT
+template <typename R>
+__global__ void __launch_bounds__(kThreads2) mci2_rowfwd(const R* __restrict__ in, zc<R>* __restrict__ X,
+                                                         const zc<R>* __restrict__ roots2, const Dims2 d)
+{
+    extern __shared__ __align__(16) unsigned char smem2d[];
+    const int G = d.G1, P2 = d.P2, H2 = d.H2, P1 = d.P1;
+    zc<R>* A = reinterpret_cast<zc<R>*>(smem2d);
+    zc<R>* B = A + (size_t)(G / 2) * P2;
+    const int b = blockIdx.z, m = blockIdx.y, p0 = blockIdx.x * G;
+    const R* src = in + ((int64_t)b * d.M + m) * P1 * P2 + (int64_t)p0 * P2;
+    for (int idx = threadIdx.x; idx < (G / 2) * P2; idx += blockDim.x) {
+        const int q = idx / P2, c = idx - q * P2;
+        A[idx] = zc<R>{src[(int64_t)(2 * q) * P2 + c], src[(int64_t)(2 * q + 1) * P2 + c]};
+    }
+    __syncthreads();
+    const zc<R>* res = fft_seq(A, B, P2, G / 2, roots2, false);
+    zc<R>* dst = X + ((int64_t)b * d.M + m) * (H2 + 1) * P1 + p0;
+    for (int idx = threadIdx.x; idx < (H2 + 1) * G; idx += blockDim.x) {
+        const int k2 = idx / G, g = idx - k2 * G;
+        const zc<R>* seq = res + (size_t)(g >> 1) * P2;
+        const zc<R> z = seq[k2];
+        const zc<R> zc_ = zconj(seq[k2 == 0 ? 0 : P2 - k2]);
+        // even row: (z + conj z(-k)) / 2; odd row: (z - conj z(-k)) / (2 i)
+        const zc<R> v = (g & 1) ? zc<R>{(R)0.5 * (z.im - zc_.im), (R)-0.5 * (z.re - zc_.re)}
+                                : zc<R>{(R)0.5 * (z.re + zc_.re), (R)0.5 * (z.im + zc_.im)};
+        dst[(int64_t)k2 * P1 + g] = v;
+    }
+}
+
+// -------------------------------------------------------------------------------------------
+// pass 2: column FFTs, per-residue solve, output phases, inverse column FFTs
+template <typename R>
+__global__ void __launch_bounds__(kThreads2) mci2_col(const zc<R>* __restrict__ X, zc<R>* __restrict__ Z,
+                                                      const zc<R>* __restrict__ Qt, const zc<R>* __restrict__ Fy,
+                                                      const zc<R>* __restrict__ Fx, const zc<R>* __restrict__ roots1,
+                                                      const Dims2 d)
+{
+    extern __shared__ __align__(16) unsigned char smem2d[];
+    const int M = d.M, P1 = d.P1, P2 = d.P2, H2 = d.H2, Mx = d.Mx, My = d.My;
+    const int k2 = blockIdx.x, b = blockIdx.y;
+    zc<R>* bufA = reinterpret_cast<zc<R>*>(smem2d);     // M * P1
+    zc<R>* bufB = bufA + (size_t)M * P1;                 // M * P1
+    zc<R>* Yb = bufB + (size_t)M * P1;                   // chunk * P1
+    zc<R>* Sb = Yb + (size_t)d.chunk * P1;               // chunk * P1
+    __shared__ zc<R> fx[16 * 8], fxn[16 * 8];            // Fx of this column and of -k2, per (u2, jx)
+
+    const zc<R>* src = X + (int64_t)b * M * (H2 + 1) * P1 + (int64_t)k2 * P1;
+    for (int idx = threadIdx.x; idx < M * P1; idx += blockDim.x) {
+        const int m = idx / P1, p = idx - m * P1;
+        bufA[idx] = src[(int64_t)m * (H2 + 1) * P1 + p];
+    }
+    // residues of the column: r2 for k2, r2n for -k2
+    const int r2 = (k2 - d.N1x_mod + P2) % P2;
+    const int r2n = ((P2 - k2) % P2 - d.N1x_mod + P2) % P2;
+    for (int idx = threadIdx.x; idx < d.s2 * Mx; idx += blockDim.x) {
+        const int u2 = idx / Mx, jx = idx - u2 * Mx;
+        fx[idx] = Fx[((int64_t)u2 * Mx + jx) * P2 + r2];
+        fxn[idx] = Fx[((int64_t)u2 * Mx + jx) * P2 + r2n];
+    }
+    __syncthreads();
+    zc<R>* Xs = fft_seq(bufA, bufB, P1, M, roots1, false);
+    zc<R>* As = Xs == bufA ? bufB : bufA;   // A' (aliases of -k) go to the other buffer
+    // per bin k1: A_j(k) = sum_m X_m(k) Q_r(k)[m][j] (in place over X), A'_j(k) = sum_m conj X_m(k) Q_r(-k)[m][j]
+    const zc<R>* Qc = Qt + (int64_t)r2 * P1 * M * M;
+    const zc<R>* Qn = Qt + (int64_t)r2n * P1 * M * M;
+    for (int k1 = threadIdx.x; k1 < P1; k1 += blockDim.x) {
+        zc<R> x[8];
+        for (int m = 0; m < M; ++m) x[m] = Xs[m * P1 + k1];
+        const int r1 = (k1 - d.N1y_mod + P1) % P1;
+        const int r1n = ((P1 - k1) % P1 - d.N1y_mod + P1) % P1;
+        const zc<R>* q = Qc + (int64_t)r1 * M * M;
+        const zc<R>* qn = Qn + (int64_t)r1n * M * M;
+        for (int j = 0; j < M; ++j) {
+            zc<R> a{0, 0}, an{0, 0};
+            for (int m = 0; m < M; ++m) {
+                a = zadd(a, zmul(x[m], q[m * M + j]));
+                an = zadd(an, zmul(zconj(x[m]), qn[m * M + j]));
+            }
+            Xs[j * P1 + k1] = a;
+            As[j * P1 + k1] = an;
+        }
+    }
+    __syncthreads();
+    zc<R>* out = Z + (int64_t)b * d.s2 * (H2 + 1) * d.T1 + (int64_t)k2 * d.T1;
+    for (int u2 = 0; u2 < d.s2; ++u2) {
+        for (int u0 = 0; u0 < d.s1; u0 += d.chunk) {
+            const int cnt = min(d.chunk, d.s1 - u0);
+            // Y_u(k1) = sum_j A_j Fy[u1][jy][r1] Fx[u2][jx][r2] + conj(sum_j A'_j Fy[u1][jy][r1n] Fx[u2][jx][r2n])
+            // (1 / (2 P1 P2) is folded into Q)
+            for (int idx = threadIdx.x; idx < cnt * P1; idx += blockDim.x) {
+                const int c = idx / P1, k1 = idx - c * P1, u1 = u0 + c;
+                const int r1 = (k1 - d.N1y_mod + P1) % P1;
+                const int r1n = ((P1 - k1) % P1 - d.N1y_mod + P1) % P1;
+                zc<R> y{0, 0}, yn{0, 0};
+                for (int jy = 0; jy < My; ++jy) {
+                    const zc<R> fy = Fy[((int64_t)u1 * My + jy) * P1 + r1];
+                    const zc<R> fyn = Fy[((int64_t)u1 * My + jy) * P1 + r1n];
+                    for (int jx = 0; jx < Mx; ++jx) {
+                        const int j = jy * Mx + jx;
+                        y = zadd(y, zmul(Xs[j * P1 + k1], zmul(fy, fx[u2 * Mx + jx])));
+                        yn = zadd(yn, zmul(As[j * P1 + k1], zmul(fyn, fxn[u2 * Mx + jx])));
+                    }
+                }
+                Yb[idx] = zadd(y, zconj(yn));
+            }
+            __syncthreads();
+            const zc<R>* ys = fft_seq(Yb, Sb, P1, cnt, roots1, true);
+            zc<R>* o = out + (int64_t)u2 * (H2 + 1) * d.T1;
+            for (int idx = threadIdx.x; idx < cnt * P1; idx += blockDim.x) {
+                // j1 = s1 p1 + u1 with u1 in this chunk; consecutive threads take consecutive j1
+                const int p1 = idx / cnt, c = idx - p1 * cnt;
+                o[(int64_t)p1 * d.s1 + u0 + c] = ys[(size_t)c * P1 + p1];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// -------------------------------------------------------------------------------------------
+// pass 3: inverse real FFTs along rows, two real outputs (rows j1, j1 + 1) per complex FFT
+template <typename R>
+__global__ void __launch_bounds__(kThreads2) mci2_rowinv(const zc<R>* __restrict__ Z, R* __restrict__ out,
+                                                         const zc<R>* __restrict__ roots2, const Dims2 d)
+{
+    extern __shared__ __align__(16) unsigned char smem2d[];
+    const int G = d.G3, P2 = d.P2, H2 = d.H2, T1 = d.T1, s2 = d.s2;
+    const int nseq = s2 * (G / 2);
+    zc<R>* A = reinterpret_cast<zc<R>*>(smem2d);
+    zc<R>* B = A + (size_t)nseq * P2;
+    const int b = blockIdx.y, j0 = blockIdx.x * G;
+    const zc<R>* zb = Z + (int64_t)b * s2 * (H2 + 1) * T1;
+    // sequence q = u2 * (G/2) + gp holds rows (j0 + 2 gp, j0 + 2 gp + 1) of phase u2:
+    // W(k) = S_a(k) + i S_b(k), S(k) = Z(k) for k <= H2 and conj Z(P2 - k) above
+    for (int idx = threadIdx.x; idx < nseq * P2; idx += blockDim.x) {
+        const int gp = idx % (G / 2);
+        const int rest = idx / (G / 2);
+        const int u2 = rest % s2, k = rest / s2;
+        const bool up = k > H2;
+        const int kk = up ? P2 - k : k;
+        const zc<R>* e = zb + ((int64_t)u2 * (H2 + 1) + kk) * T1 + j0 + 2 * gp;
+        zc<R> sa = e[0], sb = e[1];
+        if (up) {
+            sa.im = -sa.im;
+            sb.im = -sb.im;
+        }
+        A[(size_t)(u2 * (G / 2) + gp) * P2 + k] = zc<R>{sa.re - sb.im, sa.im + sb.re};
+    }
+    __syncthreads();
+    const zc<R>* res = fft_seq(A, B, P2, nseq, roots2, true);
+    for (int idx = threadIdx.x; idx < G * d.T2; idx += blockDim.x) {
+        const int g = idx / d.T2, j2 = idx - g * d.T2;
+        const int p2 = j2 / s2, u2 = j2 - p2 * s2;
+        const zc<R> v = res[(size_t)(u2 * (G / 2) + (g >> 1)) * P2 + p2];
+        out[((int64_t)b * T1 + j0 + g) * d.T2 + j2] = (g & 1) ? v.im : v.re;
+    }
+}
+
+template <typename R>
+mci_status set_smem_t(size_t smem1, size_t smem2, size_t smem3)
+{
+    if (cudaFuncSetAttribute(mci2_rowfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1) != cudaSuccess ||
+        cudaFuncSetAttribute(mci2_col<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) != cudaSuccess ||
+        cudaFuncSetAttribute(mci2_rowinv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3) != cudaSuccess)
+        return MCI_ERR_CUDA;
+    return MCI_OK;
+}
+
+template <typename R>
+mci_status launch_t(const Dims2& D, const mci2::Tables& t, size_t smem1, size_t smem2, size_t smem3, const void* in,
+                    void* out, int64_t batch, cudaStream_t st)
+{
+    const dim3 blk(kThreads2);
+    mci2_rowfwd<R><<<dim3(D.P1 / D.G1, D.M, (unsigned)batch), blk, smem1, st>>>(
+        static_cast<const R*>(in), static_cast<zc<R>*>(t.X), static_cast<const zc<R>*>(t.roots2), D);
+    mci2_col<R><<<dim3(D.H2 + 1, (unsigned)batch), blk, smem2, st>>>(
+        static_cast<const zc<R>*>(t.X), static_cast<zc<R>*>(t.Zw), static_cast<const zc<R>*>(t.Qt),
+        static_cast<const zc<R>*>(t.Fy), static_cast<const zc<R>*>(t.Fx), static_cast<const zc<R>*>(t.roots1), D);
+    mci2_rowinv<R><<<dim3(D.T1 / D.G3, (unsigned)batch), blk, smem3, st>>>(
+        static_cast<const zc<R>*>(t.Zw), static_cast<R*>(out), static_cast<const zc<R>*>(t.roots2), D);
+    return cudaGetLastError() == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+}
+
+}  // namespace
+
+namespace mci2 {
+
+mci_status set_smem(int precision, size_t smem1, size_t smem2, size_t smem3)
+{
+    return precision == MCI_FP64 ? set_smem_t<double>(smem1, smem2, smem3) : set_smem_t<float>(smem1, smem2, smem3);
+}
+
+mci_status launch(int precision, const Dims2& d, const Tables& t, size_t smem1, size_t smem2, size_t smem3,
+                  const void* in, void* out, int64_t batch, cudaStream_t st)
+{
+    return precision == MCI_FP64 ? launch_t<double>(d, t, smem1, smem2, smem3, in, out, batch, st)
+                                 : launch_t<float>(d, t, smem1, smem2, smem3, in, out, batch, st);
+}
+
+}  // namespace mci2

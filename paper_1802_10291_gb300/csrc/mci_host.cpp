@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "mci_internal.h"
+#include "mci_linalg.h"
 
 using cd = std::complex<double>;
 
@@ -139,42 +140,19 @@ mci_status invert_residues(const mci_desc& d, int P, int64_t N1, const double* c
 {
     const int M = d.M;
     out.Q.assign((size_t)P * M * M, 0.0);
-    std::vector<cd> H(M * M), V;
+    std::vector<cd> H(M * M);
     for (int r = 0; r < P; ++r) {
         const int64_t n = N1 + r;
         for (int j = 0; j < M; ++j)
             for (int k = 0; k < M; ++k)
                 H[j * M + k] = system_multiplier(d.sys[k], custom[k], N1, n + (int64_t)j * P);
-        jacobi_svd(M, H, V);
-        std::vector<double> sig(M);
-        double smax = 0.0;
-        for (int k = 0; k < M; ++k) {
-            double nn = 0.0;
-            for (int row = 0; row < M; ++row) nn += std::norm(H[row * M + k]);
-            sig[k] = std::sqrt(nn);
-            smax = std::max(smax, sig[k]);
-        }
-        double smin = smax;
-        for (int k = 0; k < M; ++k) smin = std::min(smin, sig[k]);
-        const bool singular = !(smax > 0.0) || smin < rtol * smax;
-        if (singular) {
-            ++out.n_singular;
-            if (d.singular_policy == MCI_SINGULAR_ERROR) return MCI_ERR_SINGULAR;
-            if (d.singular_policy == MCI_SINGULAR_ZERO || !(smax > 0.0)) continue;  // Q_r = 0
-        } else {
-            out.max_cond = std::max(out.max_cond, smax / smin);
-        }
-        // pinv(H) = V Sigma^+ U^H, U[:,k] = H[:,k] / sigma_k
-        for (int m = 0; m < M; ++m)
-            for (int j = 0; j < M; ++j) {
-                cd acc = 0.0;
-                for (int k = 0; k < M; ++k) {
-                    if (!(sig[k] > rtol * smax) || sig[k] == 0.0) continue;
-                    const cd u_jk = H[j * M + k] / sig[k];
-                    acc += V[m * M + k] * std::conj(u_jk) / sig[k];
-                }
-                out.Q[((size_t)r * M + m) * M + j] = acc;
-            }
+        bool singular = false;
+        double cond = 1.0;
+        const mci_status st = invert_system(M, H, rtol, d.singular_policy, &out.Q[(size_t)r * M * M],
+                                            &singular, &cond);
+        if (st != MCI_OK) return st;
+        if (singular) ++out.n_singular;
+        else out.max_cond = std::max(out.max_cond, cond);
     }
     return MCI_OK;
 }
@@ -214,6 +192,45 @@ struct HostClass {
 };
 
 }  // namespace
+
+// Q = H^{-1} of one M x M system matrix (row-major H[j * M + k]), or its Moore-Penrose
+// pseudo-inverse V Sigma^+ U^H where sigma_min < rtol sigma_max (Remark (aequal0)); Q[m * M + j].
+mci_status invert_system(int M, std::vector<cd> H, double rtol, int policy, cd* Q, bool* singular,
+                         double* cond)
+{
+    std::vector<cd> V;
+    for (int i = 0; i < M * M; ++i) Q[i] = 0.0;
+    jacobi_svd(M, H, V);
+    std::vector<double> sig(M);
+    double smax = 0.0;
+    for (int k = 0; k < M; ++k) {
+        double nn = 0.0;
+        for (int row = 0; row < M; ++row) nn += std::norm(H[row * M + k]);
+        sig[k] = std::sqrt(nn);
+        smax = std::max(smax, sig[k]);
+    }
+    double smin = smax;
+    for (int k = 0; k < M; ++k) smin = std::min(smin, sig[k]);
+    *singular = !(smax > 0.0) || smin < rtol * smax;
+    *cond = smax > 0.0 && smin > 0.0 ? smax / smin : 0.0;
+    if (*singular) {
+        if (policy == MCI_SINGULAR_ERROR) return MCI_ERR_SINGULAR;
+        if (policy == MCI_SINGULAR_ZERO || !(smax > 0.0)) return MCI_OK;  // Q = 0
+    }
+    // U[:,k] = H[:,k] / sigma_k
+    for (int m = 0; m < M; ++m)
+        for (int j = 0; j < M; ++j) {
+            cd acc = 0.0;
+            for (int k = 0; k < M; ++k) {
+                if (!(sig[k] > rtol * smax) || sig[k] == 0.0) continue;
+                const cd u_jk = H[j * M + k] / sig[k];
+                acc += V[m * M + k] * std::conj(u_jk) / sig[k];
+            }
+            Q[m * M + j] = acc;
+        }
+    return MCI_OK;
+}
+
 }  // namespace mci
 
 using namespace mci;

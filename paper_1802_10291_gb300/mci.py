@@ -123,7 +123,7 @@ def header_functions(paths=None):
     names = set()
     for path in paths:
         text = open(path).read()
-        names |= set(re.findall(r"^\s*(?:mci_status|const char\*|int)\s+(mci_\w+)\s*\(", text, re.M))
+        names |= set(re.findall(r"^\s*(?:mci_status|const char\*|int)\s+(mci\w*)\s*\(", text, re.M))
     return sorted(names)
 
 

@@ -139,24 +139,21 @@ def channel_samples_2d(coeffs, band_y, band_x, systems, P):
 def trig_poly_2d(rng, band_y, band_x, batch=None):
     """Real 2-D trigonometric polynomial over band_y x band_x: for each pair n, -n both in the
     band, Re and Im of a(n) ~ N(0,1) / (1 + |ny| + |nx|) with a(-n) = conj a(n); a(0) ~ N(0,1);
-    frequencies whose mirror image is outside the band get 0."""
+    frequencies whose mirror image is outside the band get 0.  Both bands are contiguous."""
     by, bx = np.asarray(band_y, np.int64), np.asarray(band_x, np.int64)
     lead = () if batch is None else (batch,)
     a = np.zeros(lead + (by.size, bx.size), np.complex128)
-    iy = {int(v): i for i, v in enumerate(by)}
-    ix = {int(v): i for i, v in enumerate(bx)}
-    for y in by:
-        for x in bx:
-            y, x = int(y), int(x)
-            if -y not in iy or -x not in ix or (y, x) < (-y, -x):
-                continue
-            scale = 1.0 / (1.0 + abs(y) + abs(x))
-            if (y, x) == (0, 0):
-                a[..., iy[0], ix[0]] = rng.standard_normal(lead)
-                continue
-            z = (rng.standard_normal(lead) + 1j * rng.standard_normal(lead)) * scale
-            a[..., iy[y], ix[x]] = z
-            a[..., iy[-y], ix[-x]] = np.conj(z)
+    Y, X = np.meshgrid(by, bx, indexing="ij")
+    iy, ix = -Y - by[0], -X - bx[0]                      # index of the mirror frequency -n
+    has = (iy >= 0) & (iy < by.size) & (ix >= 0) & (ix < bx.size)
+    first = has & ((Y > 0) | ((Y == 0) & (X > 0)))       # one of each pair {n, -n}, n != 0
+    yy, xx = np.nonzero(first)
+    scale = 1.0 / (1.0 + np.abs(Y[yy, xx]) + np.abs(X[yy, xx]))
+    z = (rng.standard_normal(lead + (yy.size,)) + 1j * rng.standard_normal(lead + (yy.size,))) * scale
+    a[..., yy, xx] = z
+    a[..., iy[yy, xx], ix[yy, xx]] = np.conj(z)
+    if by[0] <= 0 <= by[-1] and bx[0] <= 0 <= bx[-1]:
+        a[..., -by[0], -bx[0]] = rng.standard_normal(lead)
     return a
 
 

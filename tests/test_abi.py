@@ -16,7 +16,8 @@ def test_exports_every_declared_symbol(mci_lib):
                              "mci_corrector_num_params", "mci_corrector_create", "mci_corrector_forward",
                              "mci_corrector_loss_grad", "mci_corrector_train_step",
                              "mci_corrector_get_state", "mci_corrector_set_state", "mci_corrector_status",
-                             "mci_corrector_destroy", "mci_generate_images", "mci_decimate", "mci_degrade"}
+                             "mci_corrector_destroy", "mci_generate_images", "mci_decimate", "mci_degrade",
+                             "mci2_plan", "mci2_interp", "mci2_plan_info", "mci2_destroy"}
     for name in declared:
         assert hasattr(mci_lib, name), name
 
@@ -99,3 +100,39 @@ def test_corrector_host_checks(mci_lib):
 def test_product_refuses_without_library(tmp_path):
     with pytest.raises(ImportError):
         mci._open(str(tmp_path / "missing.so"))
+
+
+F2, DX2, DY2 = ("identity",), ("partial", 0, 1), ("partial", 1, 0)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(systems=[F2, DX2], grid=(1, 2), P=(16, 10), T=(32, 20)), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[F2, DX2], grid=(1, 2), P=(16, 2048), T=(32, 2048)), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[F2, DX2], grid=(1, 2), P=(16, 16), T=(24, 32)), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[F2, DX2], grid=(1, 2), P=(16, 16), T=(16 * 17, 32)), mci.MCI_ERR_UNSUPPORTED_SIZE),
+    (dict(systems=[F2, DX2], grid=(0, 2), P=(16, 16), T=(32, 32)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[F2] * 9, grid=(3, 3), P=(16, 16), T=(32, 32)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[F2, ("riesz", 2)], grid=(1, 2), P=(16, 16), T=(32, 32)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[F2, ("partial", -1, 0)], grid=(1, 2), P=(16, 16), T=(32, 32)), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[F2, DX2], grid=(1, 2), P=(16, 16), T=(32, 32), max_batch=0), mci.MCI_ERR_INVALID_ARG),
+    (dict(systems=[F2, DX2], grid=(1, 2), P=(16, 16), T=(32, 32), max_batch=70000), mci.MCI_ERR_INVALID_ARG),
+])
+def test_plan_2d_validation(mci_lib, kw, status):
+    from paper_1802_10291_gb300 import mci2d
+    kw.setdefault("max_batch", 2)
+    systems = kw.pop("systems")
+    d = mci2d.make_desc(systems, kw.pop("grid"), kw.pop("P"), kw.pop("T"), **kw)
+    h = ctypes.c_void_p()
+    assert mci2d._lib().mci2_plan(ctypes.byref(h), ctypes.byref(d), None) == status
+    assert h.value is None
+
+
+def test_2d_null_arguments(mci_lib):
+    from paper_1802_10291_gb300 import mci2d
+    lib = mci2d._lib()
+    assert lib.mci2_plan(None, None, None) == mci.MCI_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert lib.mci2_plan(ctypes.byref(h), None, None) == mci.MCI_ERR_INVALID_ARG
+    assert lib.mci2_interp(None, None, None, 1, None) == mci.MCI_ERR_INVALID_ARG
+    assert lib.mci2_plan_info(None, None, None, None) == mci.MCI_ERR_INVALID_ARG
+    assert lib.mci2_destroy(None) == mci.MCI_OK
