@@ -42,60 +42,86 @@ __device__ __forceinline__ zc<R> zconj(zc<R> a) { return {a.re, -a.im}; }
 template <typename R>
 __device__ __forceinline__ zc<R> zrot(zc<R> a, bool plus_i) { return plus_i ? zc<R>{-a.im, a.re} : zc<R>{a.im, -a.re}; }
 
-// In-place-free Stockham FFT of `count` sequences of length N stored contiguously (stride N)
-// in a; b is scratch of the same size.  Forward: X_k = sum_p x_p e^{-2 pi i k p / N}; inverse:
-// the conjugate kernel, unnormalised.  roots[k] = e^{-2 pi i k / N}.  Radix 4 while 4 | rem,
-// then 2, then 3, so the stride p before every pass is a power of two.  Returns the buffer
-// holding the result.  All threads of the block must call it.
+// n / d for n d < 2^32 by a multiply-high with m = ceil(2^32 / d) (d = 1 passes n through).
+struct FDiv {
+    unsigned d, m;
+};
+__device__ __forceinline__ FDiv fdiv_make(unsigned d)
+{
+    return {d, d == 1 ? 0u : 0xFFFFFFFFu / d + 1u};   // = ceil(2^32 / d) for d > 1
+}
+__device__ __forceinline__ int fdiv(int n, FDiv f) { return f.d == 1 ? n : (int)__umulhi((unsigned)n, f.m); }
+
+// One radix-RAD Stockham pass over `count` sequences of length N (stride N): butterfly i of a
+// sequence reads x_j = src[i + j N/RAD], multiplies by w^{j k} (k = i mod p, w = e^{-+2 pi i /
+// (p RAD)}), and writes the RAD-point DFT to dst[(i / p) p RAD + k + j p].  p is a power of two
+// (2^lp).  N / RAD = 2^nb_shift * (nb_three ? 3 : 1).
+template <typename R, int RAD>
+__device__ __forceinline__ void fft_pass(const zc<R>* src, zc<R>* dst, int N, int count, int p, int lp,
+                                         int nb_shift, bool nb_three, const zc<R>* __restrict__ roots, bool inv)
+{
+    const int nb = N / RAD, step = N / (p * RAD);
+    for (int idx = threadIdx.x; idx < count * nb; idx += blockDim.x) {
+        // idx / nb: a shift, then floor(x / 3) = (x * 0xAAAAAAAB) >> 33 for 32-bit x
+        const int hi = idx >> nb_shift;
+        const int sq = nb_three ? (int)(__umulhi((unsigned)hi, 0xAAAAAAABu) >> 1) : hi;
+        const int i = idx - sq * nb;
+        const int k = i & (p - 1);
+        const zc<R>* s = src + sq * N + i;
+        zc<R>* d = dst + sq * N + ((i >> lp) * p * RAD + k);
+        zc<R> x[RAD];
+#pragma unroll
+        for (int j = 0; j < RAD; ++j) x[j] = s[j * nb];
+        if (k > 0) {
+#pragma unroll
+            for (int j = 1; j < RAD; ++j) {
+                zc<R> w = roots[j * k * step];
+                if (inv) w.im = -w.im;
+                x[j] = zmul(x[j], w);
+            }
+        }
+        if constexpr (RAD == 4) {
+            const zc<R> t0 = zadd(x[0], x[2]), t1 = zsub(x[0], x[2]);
+            const zc<R> t2 = zadd(x[1], x[3]), t3 = zsub(x[1], x[3]);
+            // forward: X1 = t1 - i t3, X3 = t1 + i t3; inverse the other way round
+            const zc<R> it3 = zrot(t3, inv);
+            d[0] = zadd(t0, t2);
+            d[p] = zadd(t1, it3);
+            d[2 * p] = zsub(t0, t2);
+            d[3 * p] = zsub(t1, it3);
+        } else if constexpr (RAD == 2) {
+            d[0] = zadd(x[0], x[1]);
+            d[p] = zsub(x[0], x[1]);
+        } else {
+            const R h = (R)0.86602540378443864676;   // sin(2 pi / 3)
+            const zc<R> t1 = zadd(x[1], x[2]), t2 = zsub(x[1], x[2]);
+            const zc<R> m = {x[0].re - (R)0.5 * t1.re, x[0].im - (R)0.5 * t1.im};
+            const zc<R> it2 = zrot(zc<R>{h * t2.re, h * t2.im}, inv);   // forward: -i h t2
+            d[0] = zadd(x[0], t1);
+            d[p] = zadd(m, it2);
+            d[2 * p] = zsub(m, it2);
+        }
+    }
+}
+
+// Stockham FFT of `count` sequences of length N stored contiguously (stride N) in a; b is
+// scratch of the same size.  Forward: X_k = sum_p x_p e^{-2 pi i k p / N}; inverse: the
+// conjugate kernel, unnormalised.  roots[k] = e^{-2 pi i k / N}.  Radix 4 while 4 | rem, then
+// 2, then 3, so the stride p before every pass is a power of two.  Returns the buffer holding
+// the result.  All threads of the block must call it, after the input is visible to all.
 template <typename R>
 __device__ zc<R>* fft_seq(zc<R>* a, zc<R>* b, int N, int count, const zc<R>* __restrict__ roots, bool inv)
 {
     zc<R>* src = a;
     zc<R>* dst = b;
+    const bool three = N % 3 == 0;
+    const int a2 = 31 - __clz(three ? N / 3 : N);   // N = 2^a2 (3 if three)
     int p = 1, lp = 0, rem = N;
     while (rem > 1) {
         const int r = rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : 3);
-        const int nb = N / r;
-        const int step = N / (p * r);
-        const int total = count * nb;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int sq = idx / nb;
-            const int i = idx - sq * nb;
-            const int k = i & (p - 1);
-            const zc<R>* s = src + (size_t)sq * N + i;
-            zc<R>* d = dst + (size_t)sq * N + ((i >> lp) * p * r + k);
-            zc<R> x[4];
-            for (int j = 0; j < r; ++j) {
-                zc<R> v = s[j * nb];
-                if (j > 0 && k > 0) {
-                    zc<R> w = roots[j * k * step];
-                    if (inv) w.im = -w.im;
-                    v = zmul(v, w);
-                }
-                x[j] = v;
-            }
-            if (r == 4) {
-                const zc<R> t0 = zadd(x[0], x[2]), t1 = zsub(x[0], x[2]);
-                const zc<R> t2 = zadd(x[1], x[3]), t3 = zsub(x[1], x[3]);
-                // forward: X1 = t1 - i t3, X3 = t1 + i t3; inverse the other way round
-                const zc<R> it3 = zrot(t3, inv);
-                d[0] = zadd(t0, t2);
-                d[p] = zadd(t1, it3);
-                d[2 * p] = zsub(t0, t2);
-                d[3 * p] = zsub(t1, it3);
-            } else if (r == 2) {
-                d[0] = zadd(x[0], x[1]);
-                d[p] = zsub(x[0], x[1]);
-            } else {
-                const R h = (R)0.86602540378443864676;   // sin(2 pi / 3)
-                const zc<R> t1 = zadd(x[1], x[2]), t2 = zsub(x[1], x[2]);
-                const zc<R> m = {x[0].re - (R)0.5 * t1.re, x[0].im - (R)0.5 * t1.im};
-                const zc<R> it2 = zrot(zc<R>{h * t2.re, h * t2.im}, inv);   // forward: -i h t2
-                d[0] = zadd(x[0], t1);
-                d[p] = zadd(m, it2);
-                d[2 * p] = zsub(m, it2);
-            }
-        }
+        if (r == 4) fft_pass<R, 4>(src, dst, N, count, p, lp, a2 - 2, three, roots, inv);
+        else if (r == 2) fft_pass<R, 2>(src, dst, N, count, p, lp, a2 - 1, three, roots, inv);
+        else fft_pass<R, 3>(src, dst, N, count, p, lp, a2, false, roots, inv);
         __syncthreads();
         zc<R>* t = src;
         src = dst;
@@ -117,17 +143,20 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowfwd(const R* __restrict__ i
     const int G = d.G1, P2 = d.P2, H2 = d.H2, P1 = d.P1;
     zc<R>* A = reinterpret_cast<zc<R>*>(smem2d);
     zc<R>* B = A + (size_t)(G / 2) * P2;
+    zc<R>* tw = B + (size_t)(G / 2) * P2;   // P2 FFT roots
+    for (int p = threadIdx.x; p < P2; p += blockDim.x) tw[p] = roots2[p];
     const int b = blockIdx.z, m = blockIdx.y, p0 = blockIdx.x * G;
     const R* src = in + ((int64_t)b * d.M + m) * P1 * P2 + (int64_t)p0 * P2;
+    const FDiv fp2 = fdiv_make(P2);
     for (int idx = threadIdx.x; idx < (G / 2) * P2; idx += blockDim.x) {
-        const int q = idx / P2, c = idx - q * P2;
+        const int q = fdiv(idx, fp2), c = idx - q * P2;
         A[idx] = zc<R>{src[(int64_t)(2 * q) * P2 + c], src[(int64_t)(2 * q + 1) * P2 + c]};
     }
     __syncthreads();
-    const zc<R>* res = fft_seq(A, B, P2, G / 2, roots2, false);
+    const zc<R>* res = fft_seq(A, B, P2, G / 2, tw, false);
     zc<R>* dst = X + ((int64_t)b * d.M + m) * (H2 + 1) * P1 + p0;
     for (int idx = threadIdx.x; idx < (H2 + 1) * G; idx += blockDim.x) {
-        const int k2 = idx / G, g = idx - k2 * G;
+        const int k2 = idx >> d.lgG1, g = idx & (G - 1);
         const zc<R>* seq = res + (size_t)(g >> 1) * P2;
         const zc<R> z = seq[k2];
         const zc<R> zc_ = zconj(seq[k2 == 0 ? 0 : P2 - k2]);
@@ -140,87 +169,104 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowfwd(const R* __restrict__ i
 
 // -------------------------------------------------------------------------------------------
 // pass 2: column FFTs, per-residue solve, output phases, inverse column FFTs
+constexpr int kMaxM = 8;
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads2) mci2_col(const zc<R>* __restrict__ X, zc<R>* __restrict__ Z,
                                                       const zc<R>* __restrict__ Qt, const zc<R>* __restrict__ Fy,
-                                                      const zc<R>* __restrict__ Fx, const zc<R>* __restrict__ roots1,
-                                                      const Dims2 d)
+                                                      const zc<R>* __restrict__ Oy, const zc<R>* __restrict__ Fx,
+                                                      const zc<R>* __restrict__ roots1, const Dims2 d)
 {
     extern __shared__ __align__(16) unsigned char smem2d[];
-    const int M = d.M, P1 = d.P1, P2 = d.P2, H2 = d.H2, Mx = d.Mx, My = d.My;
+    const int M = d.M, P1 = d.P1, P2 = d.P2, H2 = d.H2, Mx = d.Mx, s1 = d.s1;
     const int k2 = blockIdx.x, b = blockIdx.y;
     zc<R>* bufA = reinterpret_cast<zc<R>*>(smem2d);     // M * P1
     zc<R>* bufB = bufA + (size_t)M * P1;                 // M * P1
     zc<R>* Yb = bufB + (size_t)M * P1;                   // chunk * P1
     zc<R>* Sb = Yb + (size_t)d.chunk * P1;               // chunk * P1
-    __shared__ zc<R> fx[16 * 8], fxn[16 * 8];            // Fx of this column and of -k2, per (u2, jx)
+    zc<R>* tw = Sb + (size_t)d.chunk * P1;               // P1 FFT roots
+    // phase factors of the current u2 per (u1, alias j): e^{2 pi i (jy P1 u1 / T1 + n_x(j) u2 / T2)}
+    // for bin k (ph) and for bin -k (phn); the r1-dependent part Fy[u1][r1] is applied per bin
+    __shared__ zc<R> ph[16 * kMaxM], phn[16 * kMaxM];
 
     const zc<R>* src = X + (int64_t)b * M * (H2 + 1) * P1 + (int64_t)k2 * P1;
-    for (int idx = threadIdx.x; idx < M * P1; idx += blockDim.x) {
-        const int m = idx / P1, p = idx - m * P1;
-        bufA[idx] = src[(int64_t)m * (H2 + 1) * P1 + p];
-    }
+    for (int m = 0; m < M; ++m)
+        for (int p = threadIdx.x; p < P1; p += blockDim.x) bufA[m * P1 + p] = src[(int64_t)m * (H2 + 1) * P1 + p];
+    for (int p = threadIdx.x; p < P1; p += blockDim.x) tw[p] = roots1[p];
     // residues of the column: r2 for k2, r2n for -k2
-    const int r2 = (k2 - d.N1x_mod + P2) % P2;
-    const int r2n = ((P2 - k2) % P2 - d.N1x_mod + P2) % P2;
-    for (int idx = threadIdx.x; idx < d.s2 * Mx; idx += blockDim.x) {
-        const int u2 = idx / Mx, jx = idx - u2 * Mx;
-        fx[idx] = Fx[((int64_t)u2 * Mx + jx) * P2 + r2];
-        fxn[idx] = Fx[((int64_t)u2 * Mx + jx) * P2 + r2n];
-    }
+    int r2 = k2 - d.N1x_mod;
+    if (r2 < 0) r2 += P2;
+    int r2n = (k2 == 0 ? 0 : P2 - k2) - d.N1x_mod;
+    if (r2n < 0) r2n += P2;
     __syncthreads();
-    zc<R>* Xs = fft_seq(bufA, bufB, P1, M, roots1, false);
+    zc<R>* Xs = fft_seq(bufA, bufB, P1, M, tw, false);
     zc<R>* As = Xs == bufA ? bufB : bufA;   // A' (aliases of -k) go to the other buffer
     // per bin k1: A_j(k) = sum_m X_m(k) Q_r(k)[m][j] (in place over X), A'_j(k) = sum_m conj X_m(k) Q_r(-k)[m][j]
-    const zc<R>* Qc = Qt + (int64_t)r2 * P1 * M * M;
-    const zc<R>* Qn = Qt + (int64_t)r2n * P1 * M * M;
+    const zc<R>* Qc = Qt + (int64_t)r2 * M * M * P1;
+    const zc<R>* Qn = Qt + (int64_t)r2n * M * M * P1;
     for (int k1 = threadIdx.x; k1 < P1; k1 += blockDim.x) {
-        zc<R> x[8];
-        for (int m = 0; m < M; ++m) x[m] = Xs[m * P1 + k1];
-        const int r1 = (k1 - d.N1y_mod + P1) % P1;
-        const int r1n = ((P1 - k1) % P1 - d.N1y_mod + P1) % P1;
-        const zc<R>* q = Qc + (int64_t)r1 * M * M;
-        const zc<R>* qn = Qn + (int64_t)r1n * M * M;
+        zc<R> x[kMaxM];
+#pragma unroll
+        for (int m = 0; m < kMaxM; ++m) x[m] = m < M ? Xs[m * P1 + k1] : zc<R>{0, 0};
+        int r1 = k1 - d.N1y_mod;
+        if (r1 < 0) r1 += P1;
+        int r1n = (k1 == 0 ? 0 : P1 - k1) - d.N1y_mod;
+        if (r1n < 0) r1n += P1;
+        // Q is stored [r2][m][j][r1]: consecutive bins read consecutive entries
         for (int j = 0; j < M; ++j) {
             zc<R> a{0, 0}, an{0, 0};
-            for (int m = 0; m < M; ++m) {
-                a = zadd(a, zmul(x[m], q[m * M + j]));
-                an = zadd(an, zmul(zconj(x[m]), qn[m * M + j]));
+#pragma unroll
+            for (int m = 0; m < kMaxM; ++m) {
+                if (m < M) {
+                    a = zadd(a, zmul(x[m], Qc[(int64_t)(m * M + j) * P1 + r1]));
+                    an = zadd(an, zmul(zconj(x[m]), Qn[(int64_t)(m * M + j) * P1 + r1n]));
+                }
             }
             Xs[j * P1 + k1] = a;
             As[j * P1 + k1] = an;
         }
     }
-    __syncthreads();
     zc<R>* out = Z + (int64_t)b * d.s2 * (H2 + 1) * d.T1 + (int64_t)k2 * d.T1;
     for (int u2 = 0; u2 < d.s2; ++u2) {
-        for (int u0 = 0; u0 < d.s1; u0 += d.chunk) {
-            const int cnt = min(d.chunk, d.s1 - u0);
-            // Y_u(k1) = sum_j A_j Fy[u1][jy][r1] Fx[u2][jx][r2] + conj(sum_j A'_j Fy[u1][jy][r1n] Fx[u2][jx][r2n])
+        for (int idx = threadIdx.x; idx < s1 * M; idx += blockDim.x) {
+            const int u1 = idx / M, j = idx - u1 * M;
+            const int jy = j / Mx, jx = j - jy * Mx;
+            const zc<R> oy = Oy[u1 * d.My + jy];
+            ph[idx] = zmul(oy, Fx[((int64_t)u2 * Mx + jx) * P2 + r2]);
+            phn[idx] = zmul(oy, Fx[((int64_t)u2 * Mx + jx) * P2 + r2n]);
+        }
+        __syncthreads();
+        for (int u0 = 0; u0 < s1; u0 += d.chunk) {
+            const int cnt = min(d.chunk, s1 - u0);
+            // Y_u(k1) = Fy[u1][r1] sum_j A_j ph_j + conj(Fy[u1][r1n] sum_j A'_j phn_j)
             // (1 / (2 P1 P2) is folded into Q)
-            for (int idx = threadIdx.x; idx < cnt * P1; idx += blockDim.x) {
-                const int c = idx / P1, k1 = idx - c * P1, u1 = u0 + c;
-                const int r1 = (k1 - d.N1y_mod + P1) % P1;
-                const int r1n = ((P1 - k1) % P1 - d.N1y_mod + P1) % P1;
-                zc<R> y{0, 0}, yn{0, 0};
-                for (int jy = 0; jy < My; ++jy) {
-                    const zc<R> fy = Fy[((int64_t)u1 * My + jy) * P1 + r1];
-                    const zc<R> fyn = Fy[((int64_t)u1 * My + jy) * P1 + r1n];
-                    for (int jx = 0; jx < Mx; ++jx) {
-                        const int j = jy * Mx + jx;
-                        y = zadd(y, zmul(Xs[j * P1 + k1], zmul(fy, fx[u2 * Mx + jx])));
-                        yn = zadd(yn, zmul(As[j * P1 + k1], zmul(fyn, fxn[u2 * Mx + jx])));
+            for (int c = 0; c < cnt; ++c) {
+                const int u1 = u0 + c;
+                const zc<R>* f = Fy + (int64_t)u1 * P1;
+                for (int k1 = threadIdx.x; k1 < P1; k1 += blockDim.x) {
+                    int r1 = k1 - d.N1y_mod;
+                    if (r1 < 0) r1 += P1;
+                    int r1n = (k1 == 0 ? 0 : P1 - k1) - d.N1y_mod;
+                    if (r1n < 0) r1n += P1;
+                    zc<R> y{0, 0}, yn{0, 0};
+#pragma unroll
+                    for (int j = 0; j < kMaxM; ++j) {
+                        if (j < M) {
+                            y = zadd(y, zmul(Xs[j * P1 + k1], ph[u1 * M + j]));
+                            yn = zadd(yn, zmul(As[j * P1 + k1], phn[u1 * M + j]));
+                        }
                     }
+                    Yb[c * P1 + k1] = zadd(zmul(f[r1], y), zconj(zmul(f[r1n], yn)));
                 }
-                Yb[idx] = zadd(y, zconj(yn));
             }
             __syncthreads();
-            const zc<R>* ys = fft_seq(Yb, Sb, P1, cnt, roots1, true);
+            const zc<R>* ys = fft_seq(Yb, Sb, P1, cnt, tw, true);
             zc<R>* o = out + (int64_t)u2 * (H2 + 1) * d.T1;
+            const FDiv fcnt = fdiv_make(cnt);
             for (int idx = threadIdx.x; idx < cnt * P1; idx += blockDim.x) {
                 // j1 = s1 p1 + u1 with u1 in this chunk; consecutive threads take consecutive j1
-                const int p1 = idx / cnt, c = idx - p1 * cnt;
-                o[(int64_t)p1 * d.s1 + u0 + c] = ys[(size_t)c * P1 + p1];
+                const int p1 = fdiv(idx, fcnt), c = idx - p1 * cnt;
+                o[(int64_t)p1 * s1 + u0 + c] = ys[(size_t)c * P1 + p1];
             }
             __syncthreads();
         }
@@ -238,14 +284,17 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowinv(const zc<R>* __restrict
     const int nseq = s2 * (G / 2);
     zc<R>* A = reinterpret_cast<zc<R>*>(smem2d);
     zc<R>* B = A + (size_t)nseq * P2;
+    zc<R>* tw = B + (size_t)nseq * P2;   // P2 FFT roots
+    for (int p = threadIdx.x; p < P2; p += blockDim.x) tw[p] = roots2[p];
     const int b = blockIdx.y, j0 = blockIdx.x * G;
     const zc<R>* zb = Z + (int64_t)b * s2 * (H2 + 1) * T1;
     // sequence q = u2 * (G/2) + gp holds rows (j0 + 2 gp, j0 + 2 gp + 1) of phase u2:
     // W(k) = S_a(k) + i S_b(k), S(k) = Z(k) for k <= H2 and conj Z(P2 - k) above
+    const FDiv fs2 = fdiv_make(s2);
     for (int idx = threadIdx.x; idx < nseq * P2; idx += blockDim.x) {
-        const int gp = idx % (G / 2);
-        const int rest = idx / (G / 2);
-        const int u2 = rest % s2, k = rest / s2;
+        const int gp = idx & (G / 2 - 1);
+        const int rest = idx >> (d.lgG3 - 1);
+        const int k = fdiv(rest, fs2), u2 = rest - k * s2;
         const bool up = k > H2;
         const int kk = up ? P2 - k : k;
         const zc<R>* e = zb + ((int64_t)u2 * (H2 + 1) + kk) * T1 + j0 + 2 * gp;
@@ -257,12 +306,14 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowinv(const zc<R>* __restrict
         A[(size_t)(u2 * (G / 2) + gp) * P2 + k] = zc<R>{sa.re - sb.im, sa.im + sb.re};
     }
     __syncthreads();
-    const zc<R>* res = fft_seq(A, B, P2, nseq, roots2, true);
-    for (int idx = threadIdx.x; idx < G * d.T2; idx += blockDim.x) {
-        const int g = idx / d.T2, j2 = idx - g * d.T2;
-        const int p2 = j2 / s2, u2 = j2 - p2 * s2;
-        const zc<R> v = res[(size_t)(u2 * (G / 2) + (g >> 1)) * P2 + p2];
-        out[((int64_t)b * T1 + j0 + g) * d.T2 + j2] = (g & 1) ? v.im : v.re;
+    const zc<R>* res = fft_seq(A, B, P2, nseq, tw, true);
+    for (int g = 0; g < G; ++g) {
+        R* row = out + ((int64_t)b * T1 + j0 + g) * d.T2;
+        for (int j2 = threadIdx.x; j2 < d.T2; j2 += blockDim.x) {
+            const int p2 = fdiv(j2, fs2), u2 = j2 - p2 * s2;
+            const zc<R> v = res[(size_t)(u2 * (G / 2) + (g >> 1)) * P2 + p2];
+            row[j2] = (g & 1) ? v.im : v.re;
+        }
     }
 }
 
@@ -285,7 +336,8 @@ mci_status launch_t(const Dims2& D, const mci2::Tables& t, size_t smem1, size_t 
         static_cast<const R*>(in), static_cast<zc<R>*>(t.X), static_cast<const zc<R>*>(t.roots2), D);
     mci2_col<R><<<dim3(D.H2 + 1, (unsigned)batch), blk, smem2, st>>>(
         static_cast<const zc<R>*>(t.X), static_cast<zc<R>*>(t.Zw), static_cast<const zc<R>*>(t.Qt),
-        static_cast<const zc<R>*>(t.Fy), static_cast<const zc<R>*>(t.Fx), static_cast<const zc<R>*>(t.roots1), D);
+        static_cast<const zc<R>*>(t.Fy), static_cast<const zc<R>*>(t.Oy), static_cast<const zc<R>*>(t.Fx),
+        static_cast<const zc<R>*>(t.roots1), D);
     mci2_rowinv<R><<<dim3(D.T1 / D.G3, (unsigned)batch), blk, smem3, st>>>(
         static_cast<const zc<R>*>(t.Zw), static_cast<R*>(out), static_cast<const zc<R>*>(t.roots2), D);
     return cudaGetLastError() == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;

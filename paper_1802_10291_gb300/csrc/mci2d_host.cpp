@@ -71,6 +71,7 @@ struct mci2_plan_s {
     size_t csz = 8;
     void* Qt = nullptr;
     void* Fy = nullptr;
+    void* Oy = nullptr;
     void* Fx = nullptr;
     void* roots1 = nullptr;
     void* roots2 = nullptr;
@@ -105,9 +106,9 @@ mci_status build2(mci2_plan_s* p, cudaStream_t st)
     const Dims2& D = p->dims;
     const int M = D.M, P1 = D.P1, P2 = D.P2;
     const double rtol = d.singular_rtol > 0 ? d.singular_rtol : 1e-13;
-    // Q table [r2][r1][m][j] with 1 / (2 P1 P2) folded in
-    std::vector<R> Q;
-    Q.reserve((size_t)P1 * P2 * M * M * 2);
+    // Q table [r2][m][j][r1] with 1 / (2 P1 P2) folded in (bins of one column read
+    // consecutive r1)
+    std::vector<R> Q((size_t)P1 * P2 * M * M * 2);
     std::vector<cd> H(M * M), q(M * M);
     const double scale = 1.0 / (2.0 * P1 * P2);
     for (int r2 = 0; r2 < P2; ++r2)
@@ -123,13 +124,19 @@ mci_status build2(mci2_plan_s* p, cudaStream_t st)
             if (s != MCI_OK) return s;
             if (sing) ++p->n_singular;
             else p->max_cond = std::max(p->max_cond, cond);
-            for (int i = 0; i < M * M; ++i) push(Q, q[i] * scale);
+            for (int i = 0; i < M * M; ++i) {
+                const size_t e = (((size_t)r2 * M * M + i) * P1 + r1) * 2;
+                Q[e] = (R)(q[i].real() * scale);
+                Q[e + 1] = (R)(q[i].imag() * scale);
+            }
         }
     // phase factors e^{2 pi i n u / T} per axis: [u][j_axis][r]
-    std::vector<R> Fy, Fx, ro1, ro2;
+    // along y the factor splits as e^{2 pi i (N1y + r) u / T1} e^{2 pi i jy u / s1}
+    std::vector<R> Fy, Oy, Fx, ro1, ro2;
     for (int u = 0; u < D.s1; ++u)
-        for (int jy = 0; jy < D.My; ++jy)
-            for (int r = 0; r < P1; ++r) push(Fy, cis2((p->N1y + r + (int64_t)jy * P1) * u, D.T1));
+        for (int r = 0; r < P1; ++r) push(Fy, cis2((p->N1y + r) * u, D.T1));
+    for (int u = 0; u < D.s1; ++u)
+        for (int jy = 0; jy < D.My; ++jy) push(Oy, cis2((int64_t)jy * u, D.s1));
     for (int u = 0; u < D.s2; ++u)
         for (int jx = 0; jx < D.Mx; ++jx)
             for (int r = 0; r < P2; ++r) push(Fx, cis2((p->N1x + r + (int64_t)jx * P2) * u, D.T2));
@@ -138,6 +145,7 @@ mci_status build2(mci2_plan_s* p, cudaStream_t st)
     mci_status s;
     if ((s = upload(Q, &p->Qt, st)) != MCI_OK) return s;
     if ((s = upload(Fy, &p->Fy, st)) != MCI_OK) return s;
+    if ((s = upload(Oy, &p->Oy, st)) != MCI_OK) return s;
     if ((s = upload(Fx, &p->Fx, st)) != MCI_OK) return s;
     if ((s = upload(ro1, &p->roots1, st)) != MCI_OK) return s;
     if ((s = upload(ro2, &p->roots2, st)) != MCI_OK) return s;
@@ -147,8 +155,8 @@ mci_status build2(mci2_plan_s* p, cudaStream_t st)
 
 void free2(mci2_plan_s* p)
 {
-    void* bufs[7] = {p->Qt, p->Fy, p->Fx, p->roots1, p->roots2, p->X, p->Zw};
-    for (int i = 0; i < 7; ++i)
+    void* bufs[8] = {p->Qt, p->Fy, p->Oy, p->Fx, p->roots1, p->roots2, p->X, p->Zw};
+    for (int i = 0; i < 8; ++i)
         if (bufs[i]) cudaFree(bufs[i]);
     delete p;
 }
@@ -202,26 +210,29 @@ mci_status mci2_plan(mci2_plan_t* out, const mci2_desc* d, mci_stream_t stream)
     D.N1y_mod = (int)(((p->N1y % D.P1) + D.P1) % D.P1);
     D.N1x_mod = (int)(((p->N1x % D.P2) + D.P2) % D.P2);
     const size_t csz = p->csz;
-    // pass 1: G1 rows per CTA (even divisor of P1), G1 * P2 complex of shared memory
+    // pass 1: G1 rows per CTA (even divisor of P1), (G1 + 1) P2 complex of shared memory (the
+    // last P2 hold the FFT roots; likewise one extra row of roots in the other passes)
     D.G1 = 2;
     for (int g : {16, 8, 4})
         if (D.P1 % g == 0 && (size_t)g * D.P2 * csz <= 96 * 1024) {
             D.G1 = g;
             break;
         }
-    p->smem1 = (size_t)D.G1 * D.P2 * csz;
+    p->smem1 = (size_t)(D.G1 + 1) * D.P2 * csz;
     // pass 2: 2 M P1 for the spectra and 2 chunk P1 for the phase FFTs
     D.chunk = D.s1;
-    while (D.chunk > 1 && (size_t)(2 * M + 2 * D.chunk) * D.P1 * csz > (size_t)kSmemMax - 4096) --D.chunk;
-    p->smem2 = (size_t)(2 * M + 2 * D.chunk) * D.P1 * csz;
-    // pass 3: G3 output rows per CTA (even divisor of T1), G3 * s2 * P2 complex
+    while (D.chunk > 1 && (size_t)(2 * M + 2 * D.chunk + 1) * D.P1 * csz > (size_t)kSmemMax - 4096) --D.chunk;
+    p->smem2 = (size_t)(2 * M + 2 * D.chunk + 1) * D.P1 * csz;
+    // pass 3: G3 output rows per CTA (even divisor of T1), (G3 s2 + 1) P2 complex
     D.G3 = 2;
     for (int g : {8, 4})
         if (D.T1 % g == 0 && (size_t)g * D.s2 * D.P2 * csz <= 96 * 1024) {
             D.G3 = g;
             break;
         }
-    p->smem3 = D.G3 ? (size_t)D.G3 * D.s2 * D.P2 * csz : 0;
+    p->smem3 = (size_t)(D.G3 * D.s2 + 1) * D.P2 * csz;
+    D.lgG1 = 31 - __builtin_clz((unsigned)D.G1);
+    D.lgG3 = 31 - __builtin_clz((unsigned)D.G3);
     if (p->smem1 > (size_t)kSmemMax || p->smem2 > (size_t)kSmemMax - 4096 ||
         p->smem3 > (size_t)kSmemMax) {
         free2(p);
@@ -251,7 +262,7 @@ mci_status mci2_interp(mci2_plan_t p, const void* in, void* out, int64_t batch, 
     if (batch == 0) return MCI_OK;
     if (!in || !out || ((uintptr_t)in % 16) || ((uintptr_t)out % 16)) return MCI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const mci2::Tables t{p->Qt, p->Fy, p->Fx, p->roots1, p->roots2, p->X, p->Zw};
+    const mci2::Tables t{p->Qt, p->Fy, p->Oy, p->Fx, p->roots1, p->roots2, p->X, p->Zw};
     return mci2::launch(p->d.precision, p->dims, t, p->smem1, p->smem2, p->smem3, in, out, batch, st);
 }
 
