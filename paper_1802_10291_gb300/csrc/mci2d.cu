@@ -57,7 +57,7 @@ __device__ __forceinline__ int fdiv(int n, FDiv f) { return f.d == 1 ? n : (int)
 // (p RAD)}), and writes the RAD-point DFT to dst[(i / p) p RAD + k + j p].  p is a power of two
 // (2^lp).  N / RAD = 2^nb_shift * (nb_three ? 3 : 1).
 template <typename R, int RAD>
-__device__ __forceinline__ void fft_pass(const zc<R>* src, zc<R>* dst, int N, int count, int p, int lp,
+__device__ __forceinline__ void fft_pass(const zc<R>* src, zc<R>* dst, int N, int count, int ld, int p, int lp,
                                          int nb_shift, bool nb_three, const zc<R>* __restrict__ roots, bool inv)
 {
     const int nb = N / RAD, step = N / (p * RAD);
@@ -67,8 +67,8 @@ __device__ __forceinline__ void fft_pass(const zc<R>* src, zc<R>* dst, int N, in
         const int sq = nb_three ? (int)(__umulhi((unsigned)hi, 0xAAAAAAABu) >> 1) : hi;
         const int i = idx - sq * nb;
         const int k = i & (p - 1);
-        const zc<R>* s = src + sq * N + i;
-        zc<R>* d = dst + sq * N + ((i >> lp) * p * RAD + k);
+        const zc<R>* s = src + sq * ld + i;
+        zc<R>* d = dst + sq * ld + ((i >> lp) * p * RAD + k);
         zc<R> x[RAD];
 #pragma unroll
         for (int j = 0; j < RAD; ++j) x[j] = s[j * nb];
@@ -104,13 +104,13 @@ __device__ __forceinline__ void fft_pass(const zc<R>* src, zc<R>* dst, int N, in
     }
 }
 
-// Stockham FFT of `count` sequences of length N stored contiguously (stride N) in a; b is
-// scratch of the same size.  Forward: X_k = sum_p x_p e^{-2 pi i k p / N}; inverse: the
+// Stockham FFT of `count` sequences of length N stored at stride ld (>= N; N + 1 keeps
+// accesses that run across sequences off a single bank) in a; b is scratch of the same size.  Forward: X_k = sum_p x_p e^{-2 pi i k p / N}; inverse: the
 // conjugate kernel, unnormalised.  roots[k] = e^{-2 pi i k / N}.  Radix 4 while 4 | rem, then
 // 2, then 3, so the stride p before every pass is a power of two.  Returns the buffer holding
 // the result.  All threads of the block must call it, after the input is visible to all.
 template <typename R>
-__device__ zc<R>* fft_seq(zc<R>* a, zc<R>* b, int N, int count, const zc<R>* __restrict__ roots, bool inv)
+__device__ zc<R>* fft_seq(zc<R>* a, zc<R>* b, int N, int count, int ld, const zc<R>* __restrict__ roots, bool inv)
 {
     zc<R>* src = a;
     zc<R>* dst = b;
@@ -119,9 +119,9 @@ __device__ zc<R>* fft_seq(zc<R>* a, zc<R>* b, int N, int count, const zc<R>* __r
     int p = 1, lp = 0, rem = N;
     while (rem > 1) {
         const int r = rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : 3);
-        if (r == 4) fft_pass<R, 4>(src, dst, N, count, p, lp, a2 - 2, three, roots, inv);
-        else if (r == 2) fft_pass<R, 2>(src, dst, N, count, p, lp, a2 - 1, three, roots, inv);
-        else fft_pass<R, 3>(src, dst, N, count, p, lp, a2, false, roots, inv);
+        if (r == 4) fft_pass<R, 4>(src, dst, N, count, ld, p, lp, a2 - 2, three, roots, inv);
+        else if (r == 2) fft_pass<R, 2>(src, dst, N, count, ld, p, lp, a2 - 1, three, roots, inv);
+        else fft_pass<R, 3>(src, dst, N, count, ld, p, lp, a2, false, roots, inv);
         __syncthreads();
         zc<R>* t = src;
         src = dst;
@@ -142,22 +142,23 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowfwd(const R* __restrict__ i
     extern __shared__ __align__(16) unsigned char smem2d[];
     const int G = d.G1, P2 = d.P2, H2 = d.H2, P1 = d.P1;
     zc<R>* A = reinterpret_cast<zc<R>*>(smem2d);
-    zc<R>* B = A + (size_t)(G / 2) * P2;
-    zc<R>* tw = B + (size_t)(G / 2) * P2;   // P2 FFT roots
+    const int ld = P2 + 1;
+    zc<R>* B = A + (size_t)(G / 2) * ld;
+    zc<R>* tw = B + (size_t)(G / 2) * ld;   // P2 FFT roots
     for (int p = threadIdx.x; p < P2; p += blockDim.x) tw[p] = roots2[p];
     const int b = blockIdx.z, m = blockIdx.y, p0 = blockIdx.x * G;
     const R* src = in + ((int64_t)b * d.M + m) * P1 * P2 + (int64_t)p0 * P2;
     const FDiv fp2 = fdiv_make(P2);
     for (int idx = threadIdx.x; idx < (G / 2) * P2; idx += blockDim.x) {
         const int q = fdiv(idx, fp2), c = idx - q * P2;
-        A[idx] = zc<R>{src[(int64_t)(2 * q) * P2 + c], src[(int64_t)(2 * q + 1) * P2 + c]};
+        A[q * ld + c] = zc<R>{src[(int64_t)(2 * q) * P2 + c], src[(int64_t)(2 * q + 1) * P2 + c]};
     }
     __syncthreads();
-    const zc<R>* res = fft_seq(A, B, P2, G / 2, tw, false);
+    const zc<R>* res = fft_seq(A, B, P2, G / 2, ld, tw, false);
     zc<R>* dst = X + ((int64_t)b * d.M + m) * (H2 + 1) * P1 + p0;
     for (int idx = threadIdx.x; idx < (H2 + 1) * G; idx += blockDim.x) {
         const int k2 = idx >> d.lgG1, g = idx & (G - 1);
-        const zc<R>* seq = res + (size_t)(g >> 1) * P2;
+        const zc<R>* seq = res + (size_t)(g >> 1) * ld;
         const zc<R> z = seq[k2];
         const zc<R> zc_ = zconj(seq[k2 == 0 ? 0 : P2 - k2]);
         // even row: (z + conj z(-k)) / 2; odd row: (z - conj z(-k)) / (2 i)
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowfwd(const R* __restrict__ i
 constexpr int kMaxM = 8;
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads2) mci2_col(const zc<R>* __restrict__ X, zc<R>* __restrict__ Z,
+__global__ void __launch_bounds__(kThreads2, sizeof(R) == 4 ? 4 : 2) mci2_col(const zc<R>* __restrict__ X, zc<R>* __restrict__ Z,
                                                       const zc<R>* __restrict__ Qt, const zc<R>* __restrict__ Fy,
                                                       const zc<R>* __restrict__ Oy, const zc<R>* __restrict__ Fx,
                                                       const zc<R>* __restrict__ roots1, const Dims2 d)
@@ -180,18 +181,19 @@ __global__ void __launch_bounds__(kThreads2) mci2_col(const zc<R>* __restrict__ 
     extern __shared__ __align__(16) unsigned char smem2d[];
     const int M = d.M, P1 = d.P1, P2 = d.P2, H2 = d.H2, Mx = d.Mx, s1 = d.s1;
     const int k2 = blockIdx.x, b = blockIdx.y;
-    zc<R>* bufA = reinterpret_cast<zc<R>*>(smem2d);     // M * P1
-    zc<R>* bufB = bufA + (size_t)M * P1;                 // M * P1
-    zc<R>* Yb = bufB + (size_t)M * P1;                   // chunk * P1
-    zc<R>* Sb = Yb + (size_t)d.chunk * P1;               // chunk * P1
-    zc<R>* tw = Sb + (size_t)d.chunk * P1;               // P1 FFT roots
+    const int ld = P1 + 1;                               // sequence stride in shared memory
+    zc<R>* bufA = reinterpret_cast<zc<R>*>(smem2d);     // M sequences
+    zc<R>* bufB = bufA + (size_t)M * ld;                 // M sequences
+    zc<R>* Yb = bufB + (size_t)M * ld;                   // chunk sequences
+    zc<R>* Sb = Yb + (size_t)d.chunk * ld;               // chunk sequences
+    zc<R>* tw = Sb + (size_t)d.chunk * ld;               // P1 FFT roots
     // phase factors of the current u2 per (u1, alias j): e^{2 pi i (jy P1 u1 / T1 + n_x(j) u2 / T2)}
     // for bin k (ph) and for bin -k (phn); the r1-dependent part Fy[u1][r1] is applied per bin
     __shared__ zc<R> ph[16 * kMaxM], phn[16 * kMaxM];
 
     const zc<R>* src = X + (int64_t)b * M * (H2 + 1) * P1 + (int64_t)k2 * P1;
     for (int m = 0; m < M; ++m)
-        for (int p = threadIdx.x; p < P1; p += blockDim.x) bufA[m * P1 + p] = src[(int64_t)m * (H2 + 1) * P1 + p];
+        for (int p = threadIdx.x; p < P1; p += blockDim.x) bufA[m * ld + p] = src[(int64_t)m * (H2 + 1) * P1 + p];
     for (int p = threadIdx.x; p < P1; p += blockDim.x) tw[p] = roots1[p];
     // residues of the column: r2 for k2, r2n for -k2
     int r2 = k2 - d.N1x_mod;
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(kThreads2) mci2_col(const zc<R>* __restrict__ 
     int r2n = (k2 == 0 ? 0 : P2 - k2) - d.N1x_mod;
     if (r2n < 0) r2n += P2;
     __syncthreads();
-    zc<R>* Xs = fft_seq(bufA, bufB, P1, M, tw, false);
+    zc<R>* Xs = fft_seq(bufA, bufB, P1, M, ld, tw, false);
     zc<R>* As = Xs == bufA ? bufB : bufA;   // A' (aliases of -k) go to the other buffer
     // per bin k1: A_j(k) = sum_m X_m(k) Q_r(k)[m][j] (in place over X), A'_j(k) = sum_m conj X_m(k) Q_r(-k)[m][j]
     const zc<R>* Qc = Qt + (int64_t)r2 * M * M * P1;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kThreads2) mci2_col(const zc<R>* __restrict__ 
     for (int k1 = threadIdx.x; k1 < P1; k1 += blockDim.x) {
         zc<R> x[kMaxM];
 #pragma unroll
-        for (int m = 0; m < kMaxM; ++m) x[m] = m < M ? Xs[m * P1 + k1] : zc<R>{0, 0};
+        for (int m = 0; m < kMaxM; ++m) x[m] = m < M ? Xs[m * ld + k1] : zc<R>{0, 0};
         int r1 = k1 - d.N1y_mod;
         if (r1 < 0) r1 += P1;
         int r1n = (k1 == 0 ? 0 : P1 - k1) - d.N1y_mod;
@@ -222,8 +224,8 @@ __global__ void __launch_bounds__(kThreads2) mci2_col(const zc<R>* __restrict__ 
                     an = zadd(an, zmul(zconj(x[m]), Qn[(int64_t)(m * M + j) * P1 + r1n]));
                 }
             }
-            Xs[j * P1 + k1] = a;
-            As[j * P1 + k1] = an;
+            Xs[j * ld + k1] = a;
+            As[j * ld + k1] = an;
         }
     }
     zc<R>* out = Z + (int64_t)b * d.s2 * (H2 + 1) * d.T1 + (int64_t)k2 * d.T1;
@@ -252,21 +254,21 @@ __global__ void __launch_bounds__(kThreads2) mci2_col(const zc<R>* __restrict__ 
 #pragma unroll
                     for (int j = 0; j < kMaxM; ++j) {
                         if (j < M) {
-                            y = zadd(y, zmul(Xs[j * P1 + k1], ph[u1 * M + j]));
-                            yn = zadd(yn, zmul(As[j * P1 + k1], phn[u1 * M + j]));
+                            y = zadd(y, zmul(Xs[j * ld + k1], ph[u1 * M + j]));
+                            yn = zadd(yn, zmul(As[j * ld + k1], phn[u1 * M + j]));
                         }
                     }
-                    Yb[c * P1 + k1] = zadd(zmul(f[r1], y), zconj(zmul(f[r1n], yn)));
+                    Yb[c * ld + k1] = zadd(zmul(f[r1], y), zconj(zmul(f[r1n], yn)));
                 }
             }
             __syncthreads();
-            const zc<R>* ys = fft_seq(Yb, Sb, P1, cnt, tw, true);
+            const zc<R>* ys = fft_seq(Yb, Sb, P1, cnt, ld, tw, true);
             zc<R>* o = out + (int64_t)u2 * (H2 + 1) * d.T1;
             const FDiv fcnt = fdiv_make(cnt);
             for (int idx = threadIdx.x; idx < cnt * P1; idx += blockDim.x) {
                 // j1 = s1 p1 + u1 with u1 in this chunk; consecutive threads take consecutive j1
                 const int p1 = fdiv(idx, fcnt), c = idx - p1 * cnt;
-                o[(int64_t)p1 * s1 + u0 + c] = ys[(size_t)c * P1 + p1];
+                o[(int64_t)p1 * s1 + u0 + c] = ys[(size_t)c * ld + p1];
             }
             __syncthreads();
         }
@@ -282,36 +284,42 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowinv(const zc<R>* __restrict
     extern __shared__ __align__(16) unsigned char smem2d[];
     const int G = d.G3, P2 = d.P2, H2 = d.H2, T1 = d.T1, s2 = d.s2;
     const int nseq = s2 * (G / 2);
+    const int ld = P2 + 1;
     zc<R>* A = reinterpret_cast<zc<R>*>(smem2d);
-    zc<R>* B = A + (size_t)nseq * P2;
-    zc<R>* tw = B + (size_t)nseq * P2;   // P2 FFT roots
+    zc<R>* B = A + (size_t)nseq * ld;
+    zc<R>* tw = B + (size_t)nseq * ld;   // P2 FFT roots
     for (int p = threadIdx.x; p < P2; p += blockDim.x) tw[p] = roots2[p];
     const int b = blockIdx.y, j0 = blockIdx.x * G;
     const zc<R>* zb = Z + (int64_t)b * s2 * (H2 + 1) * T1;
     // sequence q = u2 * (G/2) + gp holds rows (j0 + 2 gp, j0 + 2 gp + 1) of phase u2:
-    // W(k) = S_a(k) + i S_b(k), S(k) = Z(k) for k <= H2 and conj Z(P2 - k) above
+    // W(k) = S_a(k) + i S_b(k) and W(P2 - k) = conj S_a(k) + i conj S_b(k), S = Z for k <= H2.
+    // The two rows' values are adjacent in Z (j1 contiguous): one 2-element read per stored bin.
     const FDiv fs2 = fdiv_make(s2);
-    for (int idx = threadIdx.x; idx < nseq * P2; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nseq * (H2 + 1); idx += blockDim.x) {
         const int gp = idx & (G / 2 - 1);
         const int rest = idx >> (d.lgG3 - 1);
         const int k = fdiv(rest, fs2), u2 = rest - k * s2;
-        const bool up = k > H2;
-        const int kk = up ? P2 - k : k;
-        const zc<R>* e = zb + ((int64_t)u2 * (H2 + 1) + kk) * T1 + j0 + 2 * gp;
-        zc<R> sa = e[0], sb = e[1];
-        if (up) {
-            sa.im = -sa.im;
-            sb.im = -sb.im;
+        const zc<R>* e = zb + ((int64_t)u2 * (H2 + 1) + k) * T1 + j0 + 2 * gp;
+        zc<R> sa, sb;
+        if constexpr (sizeof(R) == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(e);   // 16-byte aligned: j0 + 2 gp and T1 even
+            sa = zc<R>{v.x, v.y};
+            sb = zc<R>{v.z, v.w};
+        } else {
+            sa = e[0];
+            sb = e[1];
         }
-        A[(size_t)(u2 * (G / 2) + gp) * P2 + k] = zc<R>{sa.re - sb.im, sa.im + sb.re};
+        zc<R>* q = A + (size_t)(u2 * (G / 2) + gp) * ld;
+        q[k] = zc<R>{sa.re - sb.im, sa.im + sb.re};
+        if (k > 0 && k < H2) q[P2 - k] = zc<R>{sa.re + sb.im, -sa.im + sb.re};
     }
     __syncthreads();
-    const zc<R>* res = fft_seq(A, B, P2, nseq, tw, true);
+    const zc<R>* res = fft_seq(A, B, P2, nseq, ld, tw, true);
     for (int g = 0; g < G; ++g) {
         R* row = out + ((int64_t)b * T1 + j0 + g) * d.T2;
         for (int j2 = threadIdx.x; j2 < d.T2; j2 += blockDim.x) {
             const int p2 = fdiv(j2, fs2), u2 = j2 - p2 * s2;
-            const zc<R> v = res[(size_t)(u2 * (G / 2) + (g >> 1)) * P2 + p2];
+            const zc<R> v = res[(size_t)(u2 * (G / 2) + (g >> 1)) * ld + p2];
             row[j2] = (g & 1) ? v.im : v.re;
         }
     }

@@ -210,27 +210,28 @@ mci_status mci2_plan(mci2_plan_t* out, const mci2_desc* d, mci_stream_t stream)
     D.N1y_mod = (int)(((p->N1y % D.P1) + D.P1) % D.P1);
     D.N1x_mod = (int)(((p->N1x % D.P2) + D.P2) % D.P2);
     const size_t csz = p->csz;
-    // pass 1: G1 rows per CTA (even divisor of P1), (G1 + 1) P2 complex of shared memory (the
-    // last P2 hold the FFT roots; likewise one extra row of roots in the other passes)
+    // pass 1: G1 rows per CTA (even divisor of P1); shared memory: FFT sequences at stride
+    // P2 + 1 (G1 of them with the scratch) and P2 FFT roots, likewise in the other passes
     D.G1 = 2;
     for (int g : {16, 8, 4})
         if (D.P1 % g == 0 && (size_t)g * D.P2 * csz <= 96 * 1024) {
             D.G1 = g;
             break;
         }
-    p->smem1 = (size_t)(D.G1 + 1) * D.P2 * csz;
-    // pass 2: 2 M P1 for the spectra and 2 chunk P1 for the phase FFTs
+    p->smem1 = ((size_t)D.G1 * (D.P2 + 1) + D.P2) * csz;
+    // pass 2: 2 M sequences for the spectra and 2 chunk for the phase FFTs
     D.chunk = D.s1;
-    while (D.chunk > 1 && (size_t)(2 * M + 2 * D.chunk + 1) * D.P1 * csz > (size_t)kSmemMax - 4096) --D.chunk;
-    p->smem2 = (size_t)(2 * M + 2 * D.chunk + 1) * D.P1 * csz;
-    // pass 3: G3 output rows per CTA (even divisor of T1), (G3 s2 + 1) P2 complex
+    auto smem_col = [&](int chunk) { return ((size_t)(2 * M + 2 * chunk) * (D.P1 + 1) + D.P1) * csz; };
+    while (D.chunk > 1 && smem_col(D.chunk) > (size_t)kSmemMax - 4096) --D.chunk;
+    p->smem2 = smem_col(D.chunk);
+    // pass 3: G3 output rows per CTA (even divisor of T1), G3 s2 sequences with the scratch
     D.G3 = 2;
     for (int g : {8, 4})
         if (D.T1 % g == 0 && (size_t)g * D.s2 * D.P2 * csz <= 96 * 1024) {
             D.G3 = g;
             break;
         }
-    p->smem3 = (size_t)(D.G3 * D.s2 + 1) * D.P2 * csz;
+    p->smem3 = ((size_t)D.G3 * D.s2 * (D.P2 + 1) + D.P2) * csz;
     D.lgG1 = 31 - __builtin_clz((unsigned)D.G1);
     D.lgG3 = 31 - __builtin_clz((unsigned)D.G3);
     if (p->smem1 > (size_t)kSmemMax || p->smem2 > (size_t)kSmemMax - 4096 ||
