@@ -170,16 +170,16 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowfwd(const R* __restrict__ i
 
 // -------------------------------------------------------------------------------------------
 // pass 2: column FFTs, per-residue solve, output phases, inverse column FFTs
-constexpr int kMaxM = 8;
-
-template <typename R>
-__global__ void __launch_bounds__(kThreads2, sizeof(R) == 4 ? 4 : 2) mci2_col(const zc<R>* __restrict__ X, zc<R>* __restrict__ Z,
-                                                      const zc<R>* __restrict__ Qt, const zc<R>* __restrict__ Fy,
-                                                      const zc<R>* __restrict__ Oy, const zc<R>* __restrict__ Fx,
-                                                      const zc<R>* __restrict__ roots1, const Dims2 d)
+// (one instantiation per channel count M, so the per-bin M x M products unroll fully)
+template <typename R, int M>
+__global__ void __launch_bounds__(kThreads2, sizeof(R) == 4 ? 4 : 2)
+    mci2_col(const zc<R>* __restrict__ X, zc<R>* __restrict__ Z, const zc<R>* __restrict__ Qt,
+             const zc<R>* __restrict__ Fy, const zc<R>* __restrict__ Oy, const zc<R>* __restrict__ Fx,
+             const zc<R>* __restrict__ roots1, const Dims2 d)
 {
     extern __shared__ __align__(16) unsigned char smem2d[];
-    const int M = d.M, P1 = d.P1, P2 = d.P2, H2 = d.H2, Mx = d.Mx, s1 = d.s1;
+    const int P1 = d.P1, P2 = d.P2, H2 = d.H2, Mx = d.Mx, s1 = d.s1;
+    const int nph = s1 * d.s2;                           // output phases q = u2 s1 + u1
     const int k2 = blockIdx.x, b = blockIdx.y;
     const int ld = P1 + 1;                               // sequence stride in shared memory
     zc<R>* bufA = reinterpret_cast<zc<R>*>(smem2d);     // M sequences
@@ -187,11 +187,13 @@ __global__ void __launch_bounds__(kThreads2, sizeof(R) == 4 ? 4 : 2) mci2_col(co
     zc<R>* Yb = bufB + (size_t)M * ld;                   // chunk sequences
     zc<R>* Sb = Yb + (size_t)d.chunk * ld;               // chunk sequences
     zc<R>* tw = Sb + (size_t)d.chunk * ld;               // P1 FFT roots
-    // phase factors of the current u2 per (u1, alias j): e^{2 pi i (jy P1 u1 / T1 + n_x(j) u2 / T2)}
+    // phase factors of the batch per (phase, alias j): e^{2 pi i (jy u1 / s1 + n_x(j) u2 / T2)}
     // for bin k (ph) and for bin -k (phn); the r1-dependent part Fy[u1][r1] is applied per bin
-    __shared__ zc<R> ph[16 * kMaxM], phn[16 * kMaxM];
+    zc<R>* ph = tw + P1;                                 // chunk * M
+    zc<R>* phn = ph + (size_t)d.chunk * M;               // chunk * M
 
     const zc<R>* src = X + (int64_t)b * M * (H2 + 1) * P1 + (int64_t)k2 * P1;
+#pragma unroll
     for (int m = 0; m < M; ++m)
         for (int p = threadIdx.x; p < P1; p += blockDim.x) bufA[m * ld + p] = src[(int64_t)m * (H2 + 1) * P1 + p];
     for (int p = threadIdx.x; p < P1; p += blockDim.x) tw[p] = roots1[p];
@@ -203,75 +205,73 @@ __global__ void __launch_bounds__(kThreads2, sizeof(R) == 4 ? 4 : 2) mci2_col(co
     __syncthreads();
     zc<R>* Xs = fft_seq(bufA, bufB, P1, M, ld, tw, false);
     zc<R>* As = Xs == bufA ? bufB : bufA;   // A' (aliases of -k) go to the other buffer
-    // per bin k1: A_j(k) = sum_m X_m(k) Q_r(k)[m][j] (in place over X), A'_j(k) = sum_m conj X_m(k) Q_r(-k)[m][j]
+    // per bin k1: A_j(k) = sum_m X_m(k) Q_r(k)[m][j] (in place over X), A'_j(k) = sum_m conj X_m(k) Q_r(-k)[m][j];
+    // Q is stored [r2][m][j][r1]: consecutive bins read consecutive entries
     const zc<R>* Qc = Qt + (int64_t)r2 * M * M * P1;
     const zc<R>* Qn = Qt + (int64_t)r2n * M * M * P1;
     for (int k1 = threadIdx.x; k1 < P1; k1 += blockDim.x) {
-        zc<R> x[kMaxM];
+        zc<R> x[M];
 #pragma unroll
-        for (int m = 0; m < kMaxM; ++m) x[m] = m < M ? Xs[m * ld + k1] : zc<R>{0, 0};
+        for (int m = 0; m < M; ++m) x[m] = Xs[m * ld + k1];
         int r1 = k1 - d.N1y_mod;
         if (r1 < 0) r1 += P1;
         int r1n = (k1 == 0 ? 0 : P1 - k1) - d.N1y_mod;
         if (r1n < 0) r1n += P1;
-        // Q is stored [r2][m][j][r1]: consecutive bins read consecutive entries
+#pragma unroll
         for (int j = 0; j < M; ++j) {
             zc<R> a{0, 0}, an{0, 0};
 #pragma unroll
-            for (int m = 0; m < kMaxM; ++m) {
-                if (m < M) {
-                    a = zadd(a, zmul(x[m], Qc[(int64_t)(m * M + j) * P1 + r1]));
-                    an = zadd(an, zmul(zconj(x[m]), Qn[(int64_t)(m * M + j) * P1 + r1n]));
-                }
+            for (int m = 0; m < M; ++m) {
+                a = zadd(a, zmul(x[m], Qc[(int64_t)(m * M + j) * P1 + r1]));
+                an = zadd(an, zmul(zconj(x[m]), Qn[(int64_t)(m * M + j) * P1 + r1n]));
             }
             Xs[j * ld + k1] = a;
             As[j * ld + k1] = an;
         }
     }
     zc<R>* out = Z + (int64_t)b * d.s2 * (H2 + 1) * d.T1 + (int64_t)k2 * d.T1;
-    for (int u2 = 0; u2 < d.s2; ++u2) {
-        for (int idx = threadIdx.x; idx < s1 * M; idx += blockDim.x) {
-            const int u1 = idx / M, j = idx - u1 * M;
+    for (int q0 = 0; q0 < nph; q0 += d.chunk) {
+        const int cnt = min(d.chunk, nph - q0);
+        for (int idx = threadIdx.x; idx < cnt * M; idx += blockDim.x) {
+            const int c = idx / M, j = idx - c * M;
+            const int q = q0 + c, u2 = q / s1, u1 = q - u2 * s1;
             const int jy = j / Mx, jx = j - jy * Mx;
             const zc<R> oy = Oy[u1 * d.My + jy];
             ph[idx] = zmul(oy, Fx[((int64_t)u2 * Mx + jx) * P2 + r2]);
             phn[idx] = zmul(oy, Fx[((int64_t)u2 * Mx + jx) * P2 + r2n]);
         }
-        __syncthreads();
-        for (int u0 = 0; u0 < s1; u0 += d.chunk) {
-            const int cnt = min(d.chunk, s1 - u0);
-            // Y_u(k1) = Fy[u1][r1] sum_j A_j ph_j + conj(Fy[u1][r1n] sum_j A'_j phn_j)
-            // (1 / (2 P1 P2) is folded into Q)
-            for (int c = 0; c < cnt; ++c) {
-                const int u1 = u0 + c;
-                const zc<R>* f = Fy + (int64_t)u1 * P1;
-                for (int k1 = threadIdx.x; k1 < P1; k1 += blockDim.x) {
-                    int r1 = k1 - d.N1y_mod;
-                    if (r1 < 0) r1 += P1;
-                    int r1n = (k1 == 0 ? 0 : P1 - k1) - d.N1y_mod;
-                    if (r1n < 0) r1n += P1;
-                    zc<R> y{0, 0}, yn{0, 0};
+        __syncthreads();   // also orders the A, A' writes before the first batch
+        // Y_q(k1) = Fy[u1][r1] sum_j A_j ph_j + conj(Fy[u1][r1n] sum_j A'_j phn_j)
+        // (1 / (2 P1 P2) is folded into Q)
+        for (int c = 0; c < cnt; ++c) {
+            const int u1 = (q0 + c) % s1;
+            const zc<R>* f = Fy + (int64_t)u1 * P1;
+            const zc<R>* pc = ph + c * M;
+            const zc<R>* pn = phn + c * M;
+            for (int k1 = threadIdx.x; k1 < P1; k1 += blockDim.x) {
+                int r1 = k1 - d.N1y_mod;
+                if (r1 < 0) r1 += P1;
+                int r1n = (k1 == 0 ? 0 : P1 - k1) - d.N1y_mod;
+                if (r1n < 0) r1n += P1;
+                zc<R> y{0, 0}, yn{0, 0};
 #pragma unroll
-                    for (int j = 0; j < kMaxM; ++j) {
-                        if (j < M) {
-                            y = zadd(y, zmul(Xs[j * ld + k1], ph[u1 * M + j]));
-                            yn = zadd(yn, zmul(As[j * ld + k1], phn[u1 * M + j]));
-                        }
-                    }
-                    Yb[c * ld + k1] = zadd(zmul(f[r1], y), zconj(zmul(f[r1n], yn)));
+                for (int j = 0; j < M; ++j) {
+                    y = zadd(y, zmul(Xs[j * ld + k1], pc[j]));
+                    yn = zadd(yn, zmul(As[j * ld + k1], pn[j]));
                 }
+                Yb[c * ld + k1] = zadd(zmul(f[r1], y), zconj(zmul(f[r1n], yn)));
             }
-            __syncthreads();
-            const zc<R>* ys = fft_seq(Yb, Sb, P1, cnt, ld, tw, true);
-            zc<R>* o = out + (int64_t)u2 * (H2 + 1) * d.T1;
-            const FDiv fcnt = fdiv_make(cnt);
-            for (int idx = threadIdx.x; idx < cnt * P1; idx += blockDim.x) {
-                // j1 = s1 p1 + u1 with u1 in this chunk; consecutive threads take consecutive j1
-                const int p1 = fdiv(idx, fcnt), c = idx - p1 * cnt;
-                o[(int64_t)p1 * s1 + u0 + c] = ys[(size_t)c * ld + p1];
-            }
-            __syncthreads();
         }
+        __syncthreads();
+        const zc<R>* ys = fft_seq(Yb, Sb, P1, cnt, ld, tw, true);
+        // j1 = s1 p1 + u1 of phase column u2; within one u2, consecutive threads take consecutive j1
+        const FDiv fcnt = fdiv_make(cnt);
+        for (int idx = threadIdx.x; idx < cnt * P1; idx += blockDim.x) {
+            const int p1 = fdiv(idx, fcnt), c = idx - p1 * cnt;
+            const int q = q0 + c, u2 = q / s1, u1 = q - u2 * s1;
+            out[((int64_t)u2 * (H2 + 1)) * d.T1 + (int64_t)p1 * s1 + u1] = ys[(size_t)c * ld + p1];
+        }
+        __syncthreads();
     }
 }
 
@@ -326,10 +326,34 @@ __global__ void __launch_bounds__(kThreads2) mci2_rowinv(const zc<R>* __restrict
 }
 
 template <typename R>
+bool set_col_smem(size_t smem2)
+{
+    bool ok = true;
+    ok = ok && cudaFuncSetAttribute(mci2_col<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(mci2_col<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(mci2_col<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(mci2_col<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(mci2_col<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(mci2_col<R, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(mci2_col<R, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(mci2_col<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) == cudaSuccess;
+    return ok;
+}
+
+template <typename R, int M>
+void launch_col(const Dims2& D, const mci2::Tables& t, size_t smem2, int64_t batch, cudaStream_t st)
+{
+    mci2_col<R, M><<<dim3(D.H2 + 1, (unsigned)batch), dim3(kThreads2), smem2, st>>>(
+        static_cast<const zc<R>*>(t.X), static_cast<zc<R>*>(t.Zw), static_cast<const zc<R>*>(t.Qt),
+        static_cast<const zc<R>*>(t.Fy), static_cast<const zc<R>*>(t.Oy), static_cast<const zc<R>*>(t.Fx),
+        static_cast<const zc<R>*>(t.roots1), D);
+}
+
+template <typename R>
 mci_status set_smem_t(size_t smem1, size_t smem2, size_t smem3)
 {
     if (cudaFuncSetAttribute(mci2_rowfwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1) != cudaSuccess ||
-        cudaFuncSetAttribute(mci2_col<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) != cudaSuccess ||
+        !set_col_smem<R>(smem2) ||
         cudaFuncSetAttribute(mci2_rowinv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3) != cudaSuccess)
         return MCI_ERR_CUDA;
     return MCI_OK;
@@ -342,10 +366,16 @@ mci_status launch_t(const Dims2& D, const mci2::Tables& t, size_t smem1, size_t 
     const dim3 blk(kThreads2);
     mci2_rowfwd<R><<<dim3(D.P1 / D.G1, D.M, (unsigned)batch), blk, smem1, st>>>(
         static_cast<const R*>(in), static_cast<zc<R>*>(t.X), static_cast<const zc<R>*>(t.roots2), D);
-    mci2_col<R><<<dim3(D.H2 + 1, (unsigned)batch), blk, smem2, st>>>(
-        static_cast<const zc<R>*>(t.X), static_cast<zc<R>*>(t.Zw), static_cast<const zc<R>*>(t.Qt),
-        static_cast<const zc<R>*>(t.Fy), static_cast<const zc<R>*>(t.Oy), static_cast<const zc<R>*>(t.Fx),
-        static_cast<const zc<R>*>(t.roots1), D);
+    switch (D.M) {
+    case 1: launch_col<R, 1>(D, t, smem2, batch, st); break;
+    case 2: launch_col<R, 2>(D, t, smem2, batch, st); break;
+    case 3: launch_col<R, 3>(D, t, smem2, batch, st); break;
+    case 4: launch_col<R, 4>(D, t, smem2, batch, st); break;
+    case 5: launch_col<R, 5>(D, t, smem2, batch, st); break;
+    case 6: launch_col<R, 6>(D, t, smem2, batch, st); break;
+    case 7: launch_col<R, 7>(D, t, smem2, batch, st); break;
+    default: launch_col<R, 8>(D, t, smem2, batch, st); break;
+    }
     mci2_rowinv<R><<<dim3(D.T1 / D.G3, (unsigned)batch), blk, smem3, st>>>(
         static_cast<const zc<R>*>(t.Zw), static_cast<R*>(out), static_cast<const zc<R>*>(t.roots2), D);
     return cudaGetLastError() == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;

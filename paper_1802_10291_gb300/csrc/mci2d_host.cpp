@@ -219,10 +219,14 @@ mci_status mci2_plan(mci2_plan_t* out, const mci2_desc* d, mci_stream_t stream)
             break;
         }
     p->smem1 = ((size_t)D.G1 * (D.P2 + 1) + D.P2) * csz;
-    // pass 2: 2 M sequences for the spectra and 2 chunk for the phase FFTs
-    D.chunk = D.s1;
-    auto smem_col = [&](int chunk) { return ((size_t)(2 * M + 2 * chunk) * (D.P1 + 1) + D.P1) * csz; };
-    while (D.chunk > 1 && smem_col(D.chunk) > (size_t)kSmemMax - 4096) --D.chunk;
+    // pass 2: 2 M sequences for the spectra, 2 chunk for the phase FFTs (chunk of the s1 s2 output
+    // phases per batch), the roots and 2 chunk M phase factors; the largest chunk within 56 KB
+    // (four CTAs per SM), or one phase at a time
+    auto smem_col = [&](int chunk) {
+        return ((size_t)(2 * M + 2 * chunk) * (D.P1 + 1) + D.P1 + (size_t)2 * chunk * M) * csz;
+    };
+    D.chunk = D.s1 * D.s2;
+    while (D.chunk > 1 && smem_col(D.chunk) > (size_t)56 * 1024) --D.chunk;
     p->smem2 = smem_col(D.chunk);
     // pass 3: G3 output rows per CTA (even divisor of T1), G3 s2 sequences with the scratch
     D.G3 = 2;
@@ -234,7 +238,7 @@ mci_status mci2_plan(mci2_plan_t* out, const mci2_desc* d, mci_stream_t stream)
     p->smem3 = ((size_t)D.G3 * D.s2 * (D.P2 + 1) + D.P2) * csz;
     D.lgG1 = 31 - __builtin_clz((unsigned)D.G1);
     D.lgG3 = 31 - __builtin_clz((unsigned)D.G3);
-    if (p->smem1 > (size_t)kSmemMax || p->smem2 > (size_t)kSmemMax - 4096 ||
+    if (p->smem1 > (size_t)kSmemMax || p->smem2 > (size_t)kSmemMax ||
         p->smem3 > (size_t)kSmemMax) {
         free2(p);
         return MCI_ERR_UNSUPPORTED_SIZE;
