@@ -155,6 +155,12 @@ typedef struct {
                                 type regularisation, the unblurred model's reconstruction times
                                 (1 + lambda) conj beta(n) / (|beta(n)|^2 + lambda), which is 1
                                 at n = 0.  Plans with a blur take no mci_averaged_error.    */
+    int host_access;         /* mci_interp_1d_host only.  0: when both buffers are page-locked
+                                and mapped into the device address space (cudaHostAlloc /
+                                cudaHostRegister, as reported by cudaPointerGetAttributes), the
+                                kernels read the input and write the output in host memory
+                                directly over the host link, without staging copies; other
+                                buffers are staged.  1: always stage through device chunks.  */
 } mci_desc;
 
 typedef struct {
@@ -266,11 +272,13 @@ mci_status mci_interp_1d_noalloc(mci_plan_t plan, const void* in, const int64_t*
                                  mci_stream_t stream);
 
 /*
- * mci_interp_1d_host -- mci_interp_1d on HOST buffers (packed signals): the library
- * copies the input to the device, interpolates and copies the output back.  The batch
- * is cut into chunks of consecutive signals (about 16 MB of input each) that move
- * through three internal streams -- copy in, compute, copy out -- so that transfers in
- * both directions overlap each other and the compute.
+ * mci_interp_1d_host -- mci_interp_1d on HOST buffers (packed signals).  With
+ * mci_desc.host_access = 0 and both buffers page-locked and device-mapped, the kernels
+ * access them in place (zero copy).  Otherwise the library copies the input to the device,
+ * interpolates and copies the output back: the batch is cut into chunks of consecutive
+ * signals (about 16 MB of input each) that move through three internal streams -- copy
+ * in, compute, copy out -- so that transfers in both directions overlap each other and
+ * the compute.
  *   in, out      HOST, packed as in mci_interp_1d with NULL offsets; page-locked memory
  *                (cudaHostAlloc / registered) lets the copies run asynchronously.
  *   size_class   HOST array of batch class indices (NULL for a one-class plan).

@@ -350,6 +350,7 @@ mci_status validate(const mci_desc* d)
                               d->blur_lambda >= 0.0 && std::isfinite(d->blur_lambda)))
         return MCI_ERR_INVALID_ARG;
     if (d->complex_signal != 0 && d->complex_signal != 1) return MCI_ERR_INVALID_ARG;
+    if (d->host_access != 0 && d->host_access != 1) return MCI_ERR_INVALID_ARG;
     if (d->complex_signal && (d->channel_mode != MCI_CHANNELS_MEASURED || d->max_images > 0))
         return MCI_ERR_INVALID_ARG;
     for (int c = 0; c < d->n_sizes; ++c) {
@@ -1316,6 +1317,21 @@ mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int
     if (!in || !out || (n > 1 && !size_class)) return MCI_ERR_INVALID_ARG;
     for (int64_t b = 0; b < batch && n > 1; ++b)
         if (size_class[b] < 0 || size_class[b] >= n) return MCI_ERR_INVALID_ARG;
+    if (p->desc.host_access == 0) {
+        // page-locked, device-mapped buffers on both sides: the kernels read and write them in
+        // place over the host link (the runtime's device addresses of the two buffers)
+        cudaPointerAttributes ai{}, ao{};
+        const bool qi = cudaPointerGetAttributes(&ai, in) == cudaSuccess;
+        const bool qo = qi && cudaPointerGetAttributes(&ao, out) == cudaSuccess;
+        if (!qo) cudaGetLastError();
+        if (qo && ai.type == cudaMemoryTypeHost && ao.type == cudaMemoryTypeHost && ai.devicePointer &&
+            ao.devicePointer) {
+            const mci_status st = mci_interp_1d(p, ai.devicePointer, nullptr, ao.devicePointer, nullptr,
+                                                size_class, batch, stream);
+            if (st != MCI_OK) return st;
+            return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+        }
+    }
     auto in_len = [&](int64_t b) { return p->cdev[n > 1 ? size_class[b] : 0].in_len; };
     auto out_len = [&](int64_t b) { return p->cdev[n > 1 ? size_class[b] : 0].out_len; };
     // chunks: consecutive signals up to kChunkIn bytes of input

@@ -62,7 +62,8 @@ class mci_desc(ctypes.Structure):
                 ("max_batch", ctypes.c_int64), ("max_images", ctypes.c_int64),
                 ("max_intermediate", ctypes.c_int64), ("autotune", ctypes.c_int),
                 ("complex_signal", ctypes.c_int), ("blur_taps", ctypes.c_int),
-                ("blur_sigma", ctypes.c_double), ("blur_lambda", ctypes.c_double)]
+                ("blur_sigma", ctypes.c_double), ("blur_lambda", ctypes.c_double),
+                ("host_access", ctypes.c_int)]
 
 
 class mci_plan_stats(ctypes.Structure):
@@ -161,11 +162,13 @@ def _stream(stream):
 
 def make_desc(systems, P, T, N1=None, outputs=("f",), precision="fp32", singular="pinv",
               singular_rtol=0.0, channels="measured", max_batch=1, max_images=0,
-              max_intermediate=0, autotune=False, complex_signal=False, blur=None):
+              max_intermediate=0, autotune=False, complex_signal=False, blur=None, host_access="auto"):
     """Build an mci_desc (plus the arrays it points to, kept alive on the returned object).
     systems: list of ('identity',), ('deriv', k), ('hilbert',), ('shift', tau), ('custom', table)
     where table is a float64 array of 2*M*P_c values per size class, concatenated.
-    blur: None, or (taps, sigma[, lambda]) for the blur-aware channel model."""
+    blur: None, or (taps, sigma[, lambda]) for the blur-aware channel model.
+    host_access: 'auto' (page-locked mapped host buffers accessed in place by
+    mci_interp_1d_host) or 'staged' (always copied through device chunks)."""
     P = [int(p) for p in (P if hasattr(P, "__len__") else [P])]
     T = [int(t) for t in (T if hasattr(T, "__len__") else [T])]
     sysarr = (mci_system * len(systems))()
@@ -203,6 +206,7 @@ def make_desc(systems, P, T, N1=None, outputs=("f",), precision="fp32", singular
     d.max_intermediate = int(max_intermediate)
     d.autotune = 1 if autotune else 0
     d.complex_signal = 1 if complex_signal else 0
+    d.host_access = {"auto": 0, "staged": 1}[host_access]
     if blur is not None:
         d.blur_taps = int(blur[0])
         d.blur_sigma = float(blur[1])

@@ -29,6 +29,13 @@ def test_error_strings(mci_lib):
     assert mci.error_string(-99) == "unknown status"
 
 
+def test_plan_bad_host_access(mci_lib):
+    d = mci.make_desc([("identity",)], 16, 64, max_batch=4)
+    d.host_access = 2
+    h = ctypes.c_void_p()
+    assert mci_lib.mci_plan(ctypes.byref(h), ctypes.byref(d), None) == mci.MCI_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("kw,status", [
     (dict(systems=[], P=16, T=64), mci.MCI_ERR_INVALID_ARG),
     (dict(systems=[("identity",)] * 9, P=16, T=64), mci.MCI_ERR_INVALID_ARG),

@@ -97,12 +97,13 @@ def test_graph_capture_device_grouping(cuda_device):
     plan.close()
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_host_buffers_pipeline(cuda_device, pinned):
-    """mci_interp_1d_host: the same results as the device-buffer call, over several chunks
-    (so the three buffer slots are reused)."""
+@pytest.mark.parametrize("pinned,access", [(True, "auto"), (True, "staged"), (False, "auto")])
+def test_host_buffers_pipeline(cuda_device, pinned, access):
+    """mci_interp_1d_host: the same results as the device-buffer call, with page-locked
+    buffers accessed in place (auto) or staged over several chunks (so the three buffer
+    slots are reused), and with pageable buffers (always staged)."""
     cls, in_len, out_len, xh = _uneven(4, 6000)
-    plan = mci.Plan(SYSTEMS, PS, [4 * p for p in PS], max_batch=6000)
+    plan = mci.Plan(SYSTEMS, PS, [4 * p for p in PS], max_batch=6000, host_access=access)
     x = torch.tensor(xh, dtype=torch.float32)
     y = torch.full((int(out_len.sum()),), float("nan"), dtype=torch.float32)
     if pinned:
