@@ -117,3 +117,19 @@ def test_batch_checks(cuda_device):
     with pytest.raises(mci.MciError):
         plan.interp(x, y, batch=3)
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("grid,P,T", [((5, 1), (8, 8), (40, 16)), ((1, 7), (6, 8), (12, 56)),
+                                      ((2, 4), (8, 6), (16, 24)), ((3, 1), (12, 4), (36, 8))])
+def test_interlaced_shift_channels(cuda_device, prec, grid, P, T):
+    """Channels that are the signal shifted by (ky / (My P1), kx / (Mx P2)) of a period: the
+    samples of all channels together are those of a My P1 x Mx P2 grid, each H_r is a scaled
+    DFT matrix (well conditioned), and every channel count from 3 to 8 runs its own kernel."""
+    My, Mx = grid
+    systems = [("shift", 2 * np.pi * (j // Mx) / (My * P[0]), 2 * np.pi * (j % Mx) / (Mx * P[1]))
+               for j in range(My * Mx)]
+    g = S.rng_for(15, 5 + My * 10 + Mx).standard_normal((2, My * Mx) + P)
+    out, info = run(g, systems, grid, T, prec)
+    assert info["n_singular"] == 0
+    check(out, O2.mci2_direct(systems, grid, g, T), prec)
