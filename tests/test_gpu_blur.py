@@ -162,3 +162,28 @@ def test_blur_aware_model_raises_psnr(cuda_device):
         plan.close()
         psnr[name] = corrector.psnr(out, hr)
     assert psnr["matched"] > psnr["plain"] and psnr["perturbed"] > psnr["plain"], psnr
+
+
+@pytest.mark.parametrize("prec,blur", [("fp64", (5, 1.0, 0.0)), ("fp32", (7, 1.4, 0.1))])
+def test_blur_complex_signals_match_oracle(cuda_device, prec, blur):
+    """The blur model with complex samples and outputs (no real part): against the oracle's
+    complex sum formula with the blurred custom systems."""
+    systems, P, T = [F, D1], 64, 192
+    rng = S.rng_for(11, 9)
+    g = rng.standard_normal((3, 2, P)) + 1j * rng.standard_normal((3, 2, P))
+    cdt = {"fp64": torch.complex128, "fp32": torch.complex64}[prec]
+    plan = mci.Plan(systems, P, T, precision=prec, max_batch=3, complex_signal=True, blur=blur)
+    x = torch.tensor(g, dtype=cdt, device="cuda")
+    y = torch.full((3, 1, T), complex("nan"), dtype=cdt, device="cuda")
+    plan.interp_1d(torch.view_as_real(x), torch.view_as_real(y), batch=3)
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    plan.close()
+    got = y.cpu().numpy().astype(np.complex128)
+    ref = O.mci_direct_complex(O.blur_systems(systems, P, T, *blur), g, T)
+    assert np.all(np.isfinite(got))
+    err = np.max(np.abs(got - ref))
+    if prec == "fp64":
+        assert err <= 1e-12 * max(1.0, np.max(np.abs(ref))), err
+    else:
+        assert err <= 1e-5 * np.sqrt(np.mean(np.abs(ref) ** 2)), err
