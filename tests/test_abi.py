@@ -123,6 +123,9 @@ F2, DX2, DY2 = ("identity",), ("partial", 0, 1), ("partial", 1, 0)
     (dict(systems=[F2, ("partial", -1, 0)], grid=(1, 2), P=(16, 16), T=(32, 32)), mci.MCI_ERR_INVALID_ARG),
     (dict(systems=[F2, DX2], grid=(1, 2), P=(16, 16), T=(32, 32), max_batch=0), mci.MCI_ERR_INVALID_ARG),
     (dict(systems=[F2, DX2], grid=(1, 2), P=(16, 16), T=(32, 32), max_batch=70000), mci.MCI_ERR_INVALID_ARG),
+    # FP64, 8 channels of 1024 samples per column: the column pass needs more than 227 KB
+    (dict(systems=[F2] * 8, grid=(2, 4), P=(1024, 1024), T=(2048, 2048), precision="fp64"),
+     mci.MCI_ERR_UNSUPPORTED_SIZE),
 ])
 def test_plan_2d_validation(mci_lib, kw, status):
     from paper_1802_10291_gb300 import mci2d
