@@ -405,31 +405,48 @@ __device__ __forceinline__ void store_contig_complex(const cpx<R>* sm, const Cla
 }
 
 // Strided signals (image columns): signal g's sample p at in[base + g + p * ld]
-// (one channel).  Consecutive g are adjacent in memory, so threads run over g fastest.
+// (one channel).  Consecutive g are adjacent in memory, so threads run over g fastest:
+// thread t takes column g = t % gcount and samples p = t / gcount + j * per, per =
+// blockDim / gcount, so the loop itself has no division.
 template <typename R>
 __device__ __forceinline__ void load_cols(cpx<R>* sm, const ClassDev& c, const R* __restrict__ in,
                                           int64_t base, int64_t ld, int gcount)
 {
     const int P = c.P, sst = c.sstride;
-    const int total = P * gcount;
-    for (int i = ltid(); i < total; i += blockDim.x) {
-        const int p = i / gcount, g = i - p * gcount;
-        R* d = reinterpret_cast<R*>(&sm[g * sst + pad16(p >> 1)]);
-        d[p & 1] = __ldg(in + base + g + (int64_t)p * ld);
+    const int t = ltid(), per = blockDim.x / gcount;
+    if (t < per * gcount) {
+        const int g = t % gcount;
+        R* col = reinterpret_cast<R*>(sm + g * sst);
+        const R* src = in + base + g;
+        for (int p = t / gcount; p < P; p += per) col[2 * pad16(p >> 1) + (p & 1)] = __ldg(src + (int64_t)p * ld);
     }
 }
 
+// Output sample x = s l + u of column g is component l & 1 of element l >> 1 of phase
+// buffer u; (l, u) advance with x (no division in the loop).
 template <typename R>
 __device__ __forceinline__ void store_cols(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
                                            int64_t base, int64_t ld, int gcount)
 {
     const int T = c.T, s = c.s, npad = c.npad, sst = c.sstride;
-    const int total = T * gcount;
-    for (int i = ltid(); i < total; i += blockDim.x) {
-        const int x = i / gcount, g = i - x * gcount;
-        const int l2 = x / s, u = x - l2 * s;
-        const cpx<R> z = sm[g * sst + u * npad + pad16(l2 >> 1)];
-        out[base + g + (int64_t)x * ld] = (l2 & 1) ? z.y : z.x;
+    const int t = ltid(), per = blockDim.x / gcount;
+    if (t < per * gcount) {
+        const int g = t % gcount;
+        int x = t / gcount;
+        int l = x / s, u = x - l * s;
+        const int dl = per / s, du = per - dl * s;
+        const cpx<R>* col = sm + g * sst;
+        R* dst = out + base + g;
+        for (; x < T; x += per) {
+            const cpx<R> z = col[u * npad + pad16(l >> 1)];
+            dst[(int64_t)x * ld] = (l & 1) ? z.y : z.x;
+            l += dl;
+            u += du;
+            if (u >= s) {
+                u -= s;
+                ++l;
+            }
+        }
     }
 }
 
