@@ -43,7 +43,7 @@ CPU_PER_CLASS = 100
 
 # DRAM bytes (read + write) per signal of the timed roofline kernel (mci_kernel<float, 2048>,
 # P = 4096, M = 3, T = 16384), from one ncu capture of that launch (3201 signals:
-# 157.65 MB read + 152.22 MB written; profiles/mci_kernel_f32_n2048_p4096.md).
+# 157.65 MB read + 152.22 MB written).
 # None whenever the kernel has changed since the capture.
 ROOFLINE_TRAFFIC_PER_SIGNAL = (157651456 + 152223488) / 3201
 
@@ -73,27 +73,65 @@ def make_batch(rank: int, n_signals: int = N_SIGNALS):
                 out_off=out_off, n_in=int(in_len.sum()), n_out=int(out_len.sum()))
 
 
+# Child process that polls NVML (read-only queries) every millisecond and prints
+# "sm_mhz,max_sm_mhz,event_reason_bits" per sample; argv[1] is the GPU's PCI bus id.
+_NVML_POLLER = r"""
+import ctypes, sys, time
+nv = ctypes.CDLL("libnvidia-ml.so.1")
+assert nv.nvmlInit_v2() == 0
+h = ctypes.c_void_p()
+assert nv.nvmlDeviceGetHandleByPciBusId_v2(sys.argv[1].encode(), ctypes.byref(h)) == 0
+get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+    nv.nvmlDeviceGetCurrentClocksThrottleReasons
+cur, mx, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+while True:
+    nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(cur))
+    nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+    get_reasons(h, ctypes.byref(bits))
+    sys.stdout.write("%d,%d,%d\n" % (cur.value, mx.value, bits.value))
+    sys.stdout.flush()
+    time.sleep(0.001)
+"""
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region: the
-    sampler's first line (taken before the region starts) is awaited and then left out."""
+    """SM clocks and clock-event (throttle) reasons sampled during the timed region: every
+    millisecond through NVML in a child process (so that the launching thread shares no
+    interpreter lock with it), else every 50 ms through nvidia-smi.  The sampler's first line
+    (taken before the region starts) is awaited and then left out."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40}
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, bus_id: str = None):
         self.index = index
+        self.bus_id = bus_id
         self.proc = None
+        self.kind = None
+
+    def _start(self, cmd, kind):
+        proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        ready, _, _ = select.select([proc.stdout], [], [], 10.0)
+        if ready and proc.stdout.readline().strip():
+            self.proc, self.kind = proc, kind          # first sample: before the timed region
+            return True
+        proc.kill()
+        proc.communicate()
+        return False
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            ready, _, _ = select.select([self.proc.stdout], [], [], 5.0)
-            if ready:
-                self.proc.stdout.readline()      # sample taken before the timed region
+            if self.bus_id and self._start([sys.executable, "-c", _NVML_POLLER, self.bus_id], "nvml"):
+                return self
+        except Exception:
+            self.proc = None
+        try:
+            self._start(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                         "--format=csv,noheader,nounits", "-lms", "50"], "nvidia-smi")
         except Exception:
             self.proc = None
         return self
@@ -115,6 +153,12 @@ class ClockSampler:
         for l in getattr(self, "lines", []):
             f = [x.strip() for x in l.split(",")]
             try:
+                if self.kind == "nvml":
+                    sm.append(float(f[0]))
+                    mx.append(float(f[1]))
+                    bits = int(f[2])
+                    reasons.update(n for n, b in self.BITS.items() if bits & b)
+                    continue
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
             except (ValueError, IndexError):
@@ -124,7 +168,7 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.kind}
 
 
 def bind_host_to_gpu(torch, index: int):
@@ -585,6 +629,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     host_cpus = bind_host_to_gpu(torch, local)
+    try:
+        pr = torch.cuda.get_device_properties(local)
+        bus_id = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+    except AttributeError:
+        bus_id = None
     batch = make_batch(rank)
     n_cls = len(P_CHOICES)
     T = [S_FACTOR * p for p in P_CHOICES]
@@ -609,7 +658,7 @@ def main():
             barrier(world)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
+        with ClockSampler(local, bus_id) as clk:
             torch.cuda.nvtx.range_push("timed")     # profilers can select the timed launches
             e0.record(stream)
             for _ in range(steps):

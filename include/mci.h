@@ -248,8 +248,9 @@ mci_status mci_upsample_2d(mci_plan_t plan, const float* lr, const int64_t* lr_o
                            int64_t n_img, mci_stream_t stream);
 
 /*
- * mci_interp_1d_noalloc -- the same computation and arguments as
- * mci_interp_1d, for callers that cannot allocate device memory at the time
+ * mci_interp_1d_noalloc -- the same computation as mci_interp_1d, with the
+ * same arguments except that size_class must be in DEVICE (or managed)
+ * memory, for callers that cannot allocate device memory at the time
  * they know their batch: code running under global-mode stream capture (where
  * cudaMalloc is refused), and code whose device memory is handed out up front
  * by a framework or a fixed budget.  Such a caller creates its plan once at
@@ -264,7 +265,12 @@ mci_status mci_upsample_2d(mci_plan_t plan, const float* lr, const int64_t* lr_o
  *   capture.  All calls share the array: calls that overlap on the GPU (other
  *   streams, other threads) race on it and must be serialised by the caller.
  *   Every call rewrites all of the scratch it reads, so nothing needs clearing.
- *   batch > MCI_NOALLOC_MAX_BATCH returns MCI_ERR_UNSUPPORTED_SIZE.
+ *   The cached address belongs to the device's current context: after
+ *   cudaDeviceReset the module may load elsewhere, so a process that resets a
+ *   device must not call this entry point on that device again.
+ *   batch > MCI_NOALLOC_MAX_BATCH returns MCI_ERR_UNSUPPORTED_SIZE; a plan
+ *   with several size classes and a NULL or host-memory size_class returns
+ *   MCI_ERR_INVALID_ARG.
  */
 #define MCI_NOALLOC_MAX_BATCH 65536
 mci_status mci_interp_1d_noalloc(mci_plan_t plan, const void* in, const int64_t* in_off, void* out,

@@ -188,9 +188,17 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_split3_kernel(const GemmJob
             }
         }
     }
+    // after a timeout the committed MMAs may still write the accumulator: wait for their
+    // commit once more (bounded) and free the tensor memory only once they are done; if they
+    // never finish it stays allocated (the status word already reports the timeout)
+    __shared__ int s_drained;
+    if (s_abort) {
+        if (threadIdx.x == 0) s_drained = mbar_wait(smem_u32(&bar), phase ^ 1) ? 1 : 0;
+        __syncthreads();
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && (!s_abort || s_drained)) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTileN)
                      : "memory");
     }

@@ -1423,7 +1423,18 @@ mci_status mci_interp_1d_noalloc(mci_plan_t p, const void* in, const int64_t* in
     if (batch == 0) return MCI_OK;
     if (!in || !out) return MCI_ERR_INVALID_ARG;
     const int n = (int)p->cls.size();
-    if (n > 1 && !size_class) return MCI_ERR_INVALID_ARG;
+    if (n > 1) {
+        // the grouping kernel reads size_class on the device: a host array is refused
+        // (host-side grouping would need the plan's staging blocks, sized by max_batch)
+        if (!size_class) return MCI_ERR_INVALID_ARG;
+        cudaPointerAttributes attr{};
+        if (cudaPointerGetAttributes(&attr, size_class) != cudaSuccess) {
+            cudaGetLastError();  // clear the error of an unknown pointer
+            return MCI_ERR_INVALID_ARG;
+        }
+        if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+            return MCI_ERR_INVALID_ARG;
+    }
     cudaError_t e = cudaSuccess;
     NoAllocScratch* scratch = noalloc_scratch(&e);
     if (!scratch) return MCI_ERR_CUDA;

@@ -1,6 +1,6 @@
-// Persistent interpolation kernels, one instantiation per (precision, FFT length,
-// access pattern).  A launch serves one size class: its CTAs loop over that
-// class's tiles (G signals, image rows or image columns each).
+// Interpolation kernels, one instantiation per (precision, FFT length, access
+// pattern).  A launch serves one size class with one CTA per tile (G signals,
+// image rows or image columns each); its grid is the class's tile count.
 #pragma once
 #include "mci_tile.cuh"
 

@@ -65,6 +65,8 @@ def test_complex_trig_polynomials_exact(cuda_device, prec, systems, P, s):
     for o, op in enumerate(outs):
         l1 = np.max(np.sum(np.abs(a * O.out_operator(op, band)[None, :]), axis=1))
         _check(got[:, o], truth[:, o], prec, scale=max(1.0, l1))
+        if prec == "fp64" and op != "deriv":   # unit-scale outputs: the unscaled bound too
+            assert np.max(np.abs(got[:, o] - truth[:, o])) <= TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

@@ -72,6 +72,8 @@ def test_bandlimited_exact(cuda_device, prec, name, systems, grid, P, T):
     out, _ = run(g, systems, grid, T, prec)
     truth = S.sample_coeffs_2d(a, by, bx, T).real
     check(out, truth, prec)
+    if prec == "fp64":   # unit-scale bandlimited image: the unscaled bound holds as well
+        assert np.max(np.abs(out - truth)) <= 1e-12
 
 
 def test_singular_policies(cuda_device):
