@@ -41,11 +41,10 @@ WORKLOAD = ("batched 1-D MCI: 16384 signals, M=3 {identity, Hilbert -i sgn, deri
 # same sample gives the realised FP32/FP64 errors.
 CPU_PER_CLASS = 100
 
-# DRAM bytes (read + write) per signal of the timed roofline kernel (mci_kernel<float, 2048>,
-# P = 4096, M = 3, T = 16384), from one ncu capture of that launch (3201 signals:
-# 157.65 MB read + 152.22 MB written).
+# DRAM bytes (read + write) per signal of the timed roofline kernel (the fused radix-8
+# kernel of the P = 4096 class, M = 3, T = 16384), from one ncu capture of that launch.
 # None whenever the kernel has changed since the capture.
-ROOFLINE_TRAFFIC_PER_SIGNAL = (157651456 + 152223488) / 3201
+ROOFLINE_TRAFFIC_PER_SIGNAL = None
 
 
 def peaks():
@@ -873,7 +872,9 @@ def main():
                          "frac": k_achieved / hbm,
                          "traffic": (None if ROOFLINE_TRAFFIC_PER_SIGNAL is None
                                      else ROOFLINE_TRAFFIC_PER_SIGNAL * sel.size),
-                         "kernel": "mci_kernel<float, N=2048> (P=4096 tiles), timed alone",
+                         "kernel": ("mci_fast_kernel<2048, 3, 4, 1>" if plan4.info()["signals_per_cta"][0] == 1
+                                    and plan4.info()["smem_bytes"] == 65536 else "mci_kernel<float, 2048>")
+                                   + " (P=4096 class, 3201 signals), timed alone",
                          "bytes_per_launch": k_bytes, "ms_per_launch": k_ms,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "step_roofline": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

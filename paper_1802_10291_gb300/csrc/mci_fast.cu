@@ -1,0 +1,358 @@
+// Fused radix-8 interpolation kernel for real FP32 signals (Eq. (DFTexpression) of
+// Cheng & Kou) in size classes whose FFT length N = P/2 is a power of two.
+//
+// A tile holds G = 2048/N signals and N/8 threads serve one signal.  Thread j of a
+// signal computes butterfly j (and j + (N/8) i where a pass has radix below 8) of every
+// pass, for all M_in channels of the forward transforms and all Q = s n_out phases of
+// the inverse ones, so each twiddle is formed once and applied to every channel or phase.
+//   forward:  M_in length-N complex FFTs of the packed channels (even sample = real part,
+//             odd sample = imaginary part), Stockham passes through shared memory; the
+//             first pass reads global memory;
+//   junction: the last forward pass leaves bins k = j + (N/8) r, r < 8, in registers, and
+//             those are the elements the first inverse pass reads.  In between, each thread
+//             forms the real-input spectra X_m[k] (even/odd split of the packed FFT), the
+//             phase spectra Y_q[k] = sum_m X_m[k] W_m,q[k] (Eq. (matrixeqn1) per residue,
+//             through the plan's folded weights) and their packing for the real inverse
+//             transforms.  Both steps need the mirror bin N - k; a lane permutation puts the
+//             thread holding it in the same warp (lane ^ HALF), so it moves by warp shuffles;
+//   inverse:  Q length-N inverse FFTs; the last pass leaves output elements l = j + (N/8) t
+//             of every phase in the thread, i.e. all samples [2 s l, 2 s l + 2 s) of each
+//             output, which go to global memory directly (16-byte stores for s = 2, 4).
+// Shared memory holds M_in (forward) or Q (inverse) buffers of N complex values per signal,
+// without padding: every pass writes through an XOR swizzle of the low four index bits,
+// keyed by higher bits and chosen per (stride, radix) so that the strided writes of the pass
+// and the reads of the next pass are free of bank conflicts.  The spectra never leave the SM.
+#include "fft_device.cuh"
+#include "mci_kernels.cuh"
+
+namespace mci {
+namespace {
+
+using C = cpx<float>;
+
+// Element e of a buffer written by a pass of stride NS and radix R.
+template <int NS, int R>
+__device__ __forceinline__ int swz(int e)
+{
+    if constexpr (NS == 1) return e ^ ((e >> 4) & (R - 1));
+    else if constexpr (NS == 2) return e ^ (((e >> 4) & 7) << 1);
+    else if constexpr (NS < 16) return e ^ (((e >> 5) & 3) << 2);
+    else return e;
+}
+
+__device__ __forceinline__ C ldc(const C* p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+
+__device__ __forceinline__ C shfl_xor_c(C v, int m)
+{
+    return {__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
+}
+
+// w^r for 1 <= r < R from w (forward sign; conjugated for the inverse)
+template <int R, bool INV>
+__device__ __forceinline__ void powers(C w, C (&wp)[R])
+{
+    wp[0] = mk<float>(1.f, 0.f);
+    wp[1] = INV ? conjc(w) : w;
+#pragma unroll
+    for (int r = 2; r < R; ++r) wp[r] = (r & 1) ? cmul(wp[r - 1], wp[1]) : cmul(wp[r / 2], wp[r / 2]);
+}
+
+// Pass PS of a transform (INV: inverse) on V buffers of N complex at sm + v N.  Butterfly b
+// reads elements b + r N / R and writes element r at (b div NS) NS R + b mod NS + r NS.
+template <int N, int PS, bool INV>
+struct Pass {
+    static constexpr int R = fast_radix(N, INV, PS);
+    static constexpr int NS = fast_ns(N, INV, PS);
+    static constexpr int NB = 8 / R;      // butterflies per thread
+    static constexpr int TPS = N / 8;
+    static constexpr int ST = N / R;
+
+    // element (i, r) of thread j: butterfly j + TPS i, input r
+    template <int V>
+    static __device__ __forceinline__ void load(const C* sm, int j, C (&v)[V][8])
+    {
+        constexpr int PNS = fast_ns(N, INV, PS - 1), PR = fast_radix(N, INV, PS - 1);
+#pragma unroll
+        for (int x = 0; x < V; ++x)
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[x][i * R + r] = sm[x * N + swz<PNS, PR>(j + TPS * i + r * ST)];
+    }
+
+    template <int V>
+    static __device__ __forceinline__ void compute(C (&v)[V][8], int j, const C* tab)
+    {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            if constexpr (NS > 1) {
+                const int b = j + TPS * i;
+                C wp[R];
+                powers<R, INV>(ldc(tab + fast_tw_offset(N, INV, PS) + (b & (NS - 1))), wp);
+#pragma unroll
+                for (int x = 0; x < V; ++x)
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[x][i * R + r] = cmul(v[x][i * R + r], wp[r]);
+            }
+#pragma unroll
+            for (int x = 0; x < V; ++x) dft<R, INV>(&v[x][i * R]);
+        }
+    }
+
+    template <int V>
+    static __device__ __forceinline__ void store(C* sm, int j, const C (&v)[V][8])
+    {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int b = j + TPS * i;
+            const int d = (b & ~(NS - 1)) * R + (b & (NS - 1));
+#pragma unroll
+            for (int x = 0; x < V; ++x)
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[x * N + swz<NS, R>(d + r * NS)] = v[x][i * R + r];
+        }
+    }
+};
+
+// Passes PS .. L-2 of a transform, each: load, barrier, twiddles and DFTs, store, barrier.
+template <int N, int V, int PS, bool INV>
+__device__ __forceinline__ void middle_passes(C* sm, int j, const C* tab)
+{
+    if constexpr (PS < fast_passes(N) - 1) {
+        using PP = Pass<N, PS, INV>;
+        C v[V][8];
+        PP::template load<V>(sm, j, v);
+        __syncthreads();
+        PP::template compute<V>(v, j, tab);
+        PP::template store<V>(sm, j, v);
+        __syncthreads();
+        middle_passes<N, V, PS + 1, INV>(sm, j, tab);
+    }
+}
+
+template <int N, int MIN, int S, int NOUT>
+__global__ void __launch_bounds__(256, 2) mci_fast_kernel(const KArgs a)
+{
+    constexpr int Q = S * NOUT, QM = MIN > Q ? MIN : Q;
+    constexpr int TPS = N / 8, G = 256 / TPS, L = fast_passes(N), P = 2 * N, T = S * P;
+    constexpr int HALF = TPS >= 32 ? 16 : TPS / 2;   // lane distance of mirror partners
+    static_assert(N >= kFastMinN && N <= kFastMaxN && (N & (N - 1)) == 0, "fused path length");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int64_t s_in[kMaxTile];
+    __shared__ int64_t s_out[kMaxTile];
+    __shared__ int s_cnt;
+    const int list0 = a.mode == kModeRows ? a.sched2->row_start[a.cls] : 0;
+    const int cnt = tile_signal_offsets(a, G, blockIdx.x, list0, s_in, s_out, &s_cnt);
+    const int tid = threadIdx.x, g = tid / TPS, t = tid - g * TPS;
+    const bool active = g < cnt;
+    C* sm = reinterpret_cast<C*>(smem_raw) + g * QM * N;
+    const C* W = static_cast<const C*>(a.W);
+    const C* tab = W + a.c.tw_rel;
+    // natural butterfly index, and the permuted one of the junction: within each run of
+    // 2 HALF threads, the first half takes a = w HALF + i, the second half N/8 - a (N/16
+    // for a = 0), so that bins k and N - k sit on lanes l and l ^ HALF
+    const int jn = t;
+    int jm;
+    {
+        const int w = t / (2 * HALF), l = t - w * 2 * HALF, i = l % HALF, hi = l / HALF;
+        const int aa = w * HALF + i;
+        jm = hi ? (aa == 0 ? TPS / 2 : TPS - aa) : aa;
+    }
+
+    // ---- forward pass 0: packed channels straight from global memory ----
+    {
+        using P0 = Pass<N, 0, false>;
+        C x[MIN][8];
+        const float* src = static_cast<const float*>(a.in) + (active ? s_in[g] : 0);
+        const bool al = (reinterpret_cast<uintptr_t>(src) & 7) == 0;
+        if (active && al) {
+#pragma unroll
+            for (int m = 0; m < MIN; ++m)
+#pragma unroll
+                for (int i = 0; i < P0::NB; ++i)
+#pragma unroll
+                    for (int r = 0; r < P0::R; ++r) {
+                        const float2 z = __ldcs(reinterpret_cast<const float2*>(src + m * P) + jn + TPS * i + r * P0::ST);
+                        x[m][i * P0::R + r] = mk<float>(z.x, z.y);
+                    }
+        } else if (active) {
+#pragma unroll
+            for (int m = 0; m < MIN; ++m)
+#pragma unroll
+                for (int i = 0; i < P0::NB; ++i)
+#pragma unroll
+                    for (int r = 0; r < P0::R; ++r) {
+                        const float* e = src + m * P + 2 * (jn + TPS * i + r * P0::ST);
+                        x[m][i * P0::R + r] = mk<float>(__ldcs(e), __ldcs(e + 1));
+                    }
+        } else {
+#pragma unroll
+            for (int m = 0; m < MIN; ++m)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[m][e] = mk<float>(0.f, 0.f);
+        }
+        P0::template compute<MIN>(x, jn, tab);
+        P0::template store<MIN>(sm, jn, x);
+        __syncthreads();
+    }
+    middle_passes<N, MIN, 1, false>(sm, jn, tab);
+
+    // ---- last forward pass (permuted index), spectra, combine, first inverse pass ----
+    {
+        using PL = Pass<N, L - 1, false>;
+        static_assert(PL::R == 8, "the last forward pass is radix 8");
+        C z[MIN][8];
+        PL::template load<MIN>(sm, jm, z);
+        __syncthreads();   // the first inverse pass below overwrites these buffers
+        PL::template compute<MIN>(z, jm, tab);
+        // z[m][r] = Z_m[k], k = jm + TPS r; its mirror N - k is element 7 - r of the partner
+        // lane, except on the two self-paired lanes: jm = 0 (k = TPS r <-> TPS (8 - r)) and
+        // jm = TPS / 2 (element 7 - r of the same lane)
+        const bool self0 = jm == 0, selfh = jm == TPS / 2;
+        C wk[8];   // e^{-2 pi i k / P}
+#pragma unroll
+        for (int r = 0; r < 8; ++r) wk[r] = ldc(tab + jm + r * TPS);
+        float xN[MIN];   // X_m[N] (real), used by the jm = 0 lane
+#pragma unroll
+        for (int m = 0; m < MIN; ++m) {
+            xN[m] = z[m][0].x - z[m][0].y;
+            C zm[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const C pr = shfl_xor_c(z[m][7 - r], HALF);
+                zm[r] = self0 ? z[m][(8 - r) & 7] : (selfh ? z[m][7 - r] : pr);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                // X[k] = (Z[k] + conj Z[N-k]) / 2 + e^{-2 pi i k / P} (Z[k] - conj Z[N-k]) / (2i)
+                const C e = scale(z[m][r] + conjc(zm[r]), 0.5f);
+                const C d = z[m][r] - conjc(zm[r]);
+                z[m][r] = e + cmul(wk[r], mk<float>(0.5f * d.y, -0.5f * d.x));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            C y[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int k = jm + r * TPS;
+                C acc = cmul(z[0][r], ldc(W + (size_t)q * (N + 1) + k));
+#pragma unroll
+                for (int m = 1; m < MIN; ++m) acc = acc + cmul(z[m][r], ldc(W + (size_t)(m * Q + q) * (N + 1) + k));
+                y[r] = acc;
+            }
+            C yN = mk<float>(0.f, 0.f);   // Y_q[N], on the jm = 0 lane
+            if (self0) {
+#pragma unroll
+                for (int m = 0; m < MIN; ++m) yN = yN + scale(ldc(W + (size_t)(m * Q + q) * (N + 1) + N), xN[m]);
+            }
+            C zp[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const C pr = shfl_xor_c(y[7 - r], HALF);
+                const C ym = self0 ? (r == 0 ? yN : y[(8 - r) & 7]) : (selfh ? y[7 - r] : pr);
+                // packing for the real inverse FFT: A + i C, A = Y[k] + conj Y[N-k],
+                // C = e^{2 pi i k / P} (Y[k] - conj Y[N-k])
+                const C A = y[r] + conjc(ym);
+                const C Cc = cmulc(y[r] - conjc(ym), wk[r]);
+                zp[r] = mk<float>(A.x - Cc.y, A.y + Cc.x);
+            }
+            dft<8, true>(zp);   // inverse pass 0 (stride 1): element r of butterfly jm at 8 jm + r
+#pragma unroll
+            for (int r = 0; r < 8; ++r) sm[q * N + swz<1, 8>(8 * jm + r)] = zp[r];
+        }
+        __syncthreads();
+    }
+    middle_passes<N, Q, 1, true>(sm, jn, tab);
+
+    // ---- last inverse pass, output samples straight to global memory ----
+    {
+        using PL = Pass<N, L - 1, true>;
+        C y[Q][8];
+        PL::template load<Q>(sm, jn, y);
+        PL::template compute<Q>(y, jn, tab);
+        // all lanes take part in the shuffles below; only active signals store
+        float* dst0 = static_cast<float*>(a.out) + (active ? s_out[g] : 0);
+        // element l of phase buffer (o, u) holds samples s (2l) + u (real part) and
+        // s (2l + 1) + u (imaginary part) of output o
+        const bool al = (reinterpret_cast<uintptr_t>(dst0) & ((S % 2) == 0 ? 15 : 7)) == 0;
+#pragma unroll
+        for (int i = 0; i < PL::NB; ++i)
+#pragma unroll
+            for (int r = 0; r < PL::R; ++r) {
+                const int l = jn + TPS * i + r * PL::ST;
+                const int e = i * PL::R + r;
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    const C* ph = &y[o * S][0];   // phase u of output o: ph[u * 8 + e]
+                    if constexpr (S == 4) {
+                        // the WG = min(32, N/8) lanes of a signal in this warp hold WG consecutive
+                        // l, i.e. 32 WG contiguous bytes; store h writes the h-th half of them:
+                        // lane x takes half (x & 1) of element WG h / 2 + x / 2, received by shuffles
+                        constexpr int WG = TPS < 32 ? TPS : 32;
+                        const int lane = threadIdx.x & 31, x = lane & (WG - 1);
+                        const float4 re = make_float4(ph[e].x, ph[8 + e].x, ph[16 + e].x, ph[24 + e].x);
+                        const float4 im = make_float4(ph[e].y, ph[8 + e].y, ph[16 + e].y, ph[24 + e].y);
+                        float4* wbase = reinterpret_cast<float4*>(dst0 + (size_t)o * T + 2 * S * (l - x));
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int src = (lane - x) + (WG / 2) * h + (x >> 1);
+                            const float4 lo = make_float4(__shfl_sync(0xffffffffu, re.x, src), __shfl_sync(0xffffffffu, re.y, src),
+                                                          __shfl_sync(0xffffffffu, re.z, src), __shfl_sync(0xffffffffu, re.w, src));
+                            const float4 hi = make_float4(__shfl_sync(0xffffffffu, im.x, src), __shfl_sync(0xffffffffu, im.y, src),
+                                                          __shfl_sync(0xffffffffu, im.z, src), __shfl_sync(0xffffffffu, im.w, src));
+                            if (al && active) __stcs(wbase + WG * h + x, (x & 1) ? hi : lo);
+                        }
+                        if (al) continue;
+                    } else if constexpr (S == 2) {
+                        if (al) {
+                            if (active)
+                                __stcs(reinterpret_cast<float4*>(dst0 + (size_t)o * T + 2 * S * l),
+                                       make_float4(ph[e].x, ph[8 + e].x, ph[e].y, ph[8 + e].y));
+                            continue;
+                        }
+                    }
+                    if (!active) continue;
+                    float* dst = dst0 + (size_t)o * T + 2 * S * l;
+#pragma unroll
+                    for (int u = 0; u < S; ++u) {
+                        dst[u] = ph[u * 8 + e].x;
+                        dst[S + u] = ph[u * 8 + e].y;
+                    }
+                }
+            }
+    }
+}
+
+}  // namespace
+
+#define MCI_FAST_VARIANTS(X) \
+    X(128, 3, 4, 1) X(256, 3, 4, 1) X(512, 3, 4, 1) X(1024, 3, 4, 1) X(2048, 3, 4, 1)
+
+const void* fast_kernel_lookup(int N, int M_in, int s, int n_out)
+{
+#define MCI_FAST_CASE(n, m, sc, no) \
+    if (N == n && M_in == m && s == sc && n_out == no) return (const void*)mci_fast_kernel<n, m, sc, no>;
+    MCI_FAST_VARIANTS(MCI_FAST_CASE)
+#undef MCI_FAST_CASE
+    return nullptr;
+}
+
+// Device-side launch of a fused-path class (dynamic parallelism, from the scheduler).
+__device__ bool device_launch_fast(const ClassDev& c, int grid, int smem, const KArgs& a)
+{
+#define MCI_FAST_DCASE(n, m, sc, no)                                                          \
+    if (c.N == n && c.M_in == m && c.s == sc && c.n_out == no) {                               \
+        mci_fast_kernel<n, m, sc, no><<<grid, 256, smem, cudaStreamFireAndForget>>>(a);        \
+        return true;                                                                          \
+    }
+    MCI_FAST_VARIANTS(MCI_FAST_DCASE)
+#undef MCI_FAST_DCASE
+    return false;
+}
+
+}  // namespace mci

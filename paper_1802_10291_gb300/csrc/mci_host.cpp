@@ -516,6 +516,18 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
             }
         }
         for (const cd& z : planes) push_cpx(W, z);
+        if (cd_.fast) {
+            // fused-path table: e^{-2 pi i k / P}, k = 0..N, then the per-pass twiddles
+            // e^{-2 pi i jm / (NS R)}, jm < NS, of the forward and the inverse transform
+            if ((W.size() / 2) % 2) push_cpx(W, cd(0.0));
+            cd_.tw_rel = (int)((int64_t)(W.size() / 2) - cd_.w_off);
+            for (int k = 0; k <= N; ++k) push_cpx(W, cis_frac(-(int64_t)k, P));
+            for (int inv = 0; inv < 2; ++inv)
+                for (int ps = 1; ps < fast_passes(N); ++ps) {
+                    const int ns = fast_ns(N, inv, ps), rad = fast_radix(N, inv, ps);
+                    for (int jm = 0; jm < ns; ++jm) push_cpx(W, cis_frac(-(int64_t)jm, (int64_t)ns * rad));
+                }
+        }
         if (gemm) {
             // out[s l + u] = sum_p kappa_u[(l - p) mod P] x[p], kappa_u[d] = sum over all P bins of
             // W_k[u] e^{2 pi i k d / P} with W_{P-k} = conj W_k (the kernel's real inverse FFT)
@@ -832,6 +844,7 @@ static cudaError_t autotune_tiles(mci_plan_s* p, int smem_cap, cudaStream_t s)
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     for (int c = 0; c < n && e == cudaSuccess; ++c) {
         ClassDev cd = p->cdev[c];
+        if (cd.fast) continue;   // the fused kernel's tile is fixed by N
         const int per = cd.sstride * csz;
         const int twb = smem_twiddle_count(cd.N) * csz;
         const int64_t sig_bytes = (cd.in_len + cd.out_len) * (int64_t)p->elem;
@@ -950,6 +963,12 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         cd_.chan_len = hc.P * (d.complex_signal ? 2 : 1);
         cd_.in_len = (int64_t)cd_.M_in * cd_.chan_len;
         cd_.out_len = (int64_t)cd_.n_out * hc.T * (d.complex_signal ? 2 : 1);
+        // fused radix-8 kernel: real FP32 1-D classes with N a power of two in its range and a
+        // compiled (channels, scale, outputs) variant; its tile and shared memory are fixed
+        cd_.fast = d.precision == MCI_FP32 && !d.complex_signal && d.max_images == 0 &&
+                   hc.N >= kFastMinN && hc.N <= kFastMaxN && (hc.N & (hc.N - 1)) == 0 &&
+                   fast_kernel_lookup(hc.N, cd_.M_in, hc.s, p->n_out) != nullptr;
+        if (cd_.fast) continue;
         const int per = cd_.sstride * csz + smem_twiddle_count(hc.N) * csz;
         if (per > smem_cap) {
             delete p;
@@ -961,6 +980,12 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     p->csmem.resize(n);
     for (int c = 0; c < n; ++c) {
         ClassDev& cd_ = p->cdev[c];
+        if (cd_.fast) {   // 2048 / N signals of QM buffers of N complex values
+            cd_.G = 2048 / cd_.N;
+            p->csmem[c] = cd_.G * cd_.QM * cd_.N * csz;
+            p->smem = std::max(p->smem, p->csmem[c]);
+            continue;
+        }
         const int per = cd_.sstride * csz;
         const int twb = smem_twiddle_count(cd_.N) * csz;   // FFT twiddles after the buffers
         cd_.G = std::max(1, std::min(kMaxTile, (budget - twb) / per));
@@ -1012,7 +1037,8 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         L.W = (const char*)p->d_W + p->cdev[c].w_off * 2 * p->elem;
         L.prec = d.precision;
         L.smem = p->csmem[c];
-        p->kern[c] = kernel_lookup(d.precision, false, p->cdev[c].N);
+        p->kern[c] = p->cdev[c].fast ? fast_kernel_lookup(p->cdev[c].N, p->cdev[c].M_in, p->cdev[c].s, p->n_out)
+                                     : kernel_lookup(d.precision, false, p->cdev[c].N);
         p->kern_cols[c] = d.precision == MCI_FP32 ? kernel_lookup(d.precision, true, p->cdev[c].N) : nullptr;
         if (!p->kern[c]) e = cudaErrorInvalidDeviceFunction;
         // The dynamic shared-memory limit is an attribute of the kernel function, which
@@ -1025,9 +1051,16 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared);
+            // the fused kernel runs two CTAs per SM (registers): shared memory for exactly
+            // those, the rest of the SM's storage to L1 (the bin weights and twiddles are read
+            // through it; measured 10% faster than the largest carveout); others: largest
+            int carve = cudaSharedmemCarveoutMaxShared;
+            if (k == p->kern[c] && p->cdev[c].fast) {
+                const int need = 2 * (p->csmem[c] + (int)fa.sharedSizeBytes + 1024);
+                carve = std::min(100, (100 * need + (int)prop.sharedMemPerMultiprocessor - 1) /
+                                          (int)prop.sharedMemPerMultiprocessor);
+            }
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
         }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_launch, p->launch.data(), sizeof(ClassLaunch) * n, cudaMemcpyHostToDevice, s);

@@ -60,6 +60,47 @@ MCI_HD constexpr int smem_twiddle_offset(int n, int NS)
 }
 MCI_HD constexpr int smem_twiddle_count(int n) { return smem_twiddle_offset(n, n); }
 
+// ---------------------------------------------------------------------------
+// Fused radix-8 path (mci_fast.cu) for real FP32 classes with N = P/2 a power of
+// two in [kFastMinN, kFastMaxN]: N/8 threads per signal, 2048/N signals per CTA.
+// A transform of length N = 2^n takes ceil(n/3) passes of radix 8; the leftover
+// factor 2^(n mod 3) is the first forward pass and the last inverse pass.
+constexpr int kFastMinN = 128;
+constexpr int kFastMaxN = 2048;
+MCI_HD constexpr int ilog2(int n)
+{
+    int k = 0;
+    while ((2 << k) <= n) ++k;
+    return k;
+}
+MCI_HD constexpr int fast_passes(int N) { return (ilog2(N) + 2) / 3; }
+MCI_HD constexpr int fast_radix(int N, int inv, int p)
+{
+    return ilog2(N) % 3 == 0 ? 8 : (p == (inv ? fast_passes(N) - 1 : 0) ? (1 << (ilog2(N) % 3)) : 8);
+}
+// stride NS of pass p: the product of the radices of the passes before it
+MCI_HD constexpr int fast_ns(int N, int inv, int p)
+{
+    int ns = 1;
+    for (int i = 0; i < p; ++i) ns *= fast_radix(N, inv, i);
+    return ns;
+}
+// Per-class table of the fused path (complex, after the class's bin weights):
+// e^{-2 pi i k / P} for k = 0..N, then for the forward (inv = 0) and the inverse
+// (inv = 1) transform the NS entries e^{-2 pi i jm / (NS R)}, jm < NS, of every
+// pass p >= 1 in order.  fast_tw_offset(N, 2, 0) is the table length.
+MCI_HD constexpr int fast_tw_offset(int N, int inv, int p)
+{
+    int off = N + 1;
+    for (int t = 0; t < 2; ++t)
+        for (int q = 1; q < fast_passes(N); ++q) {
+            if (t == inv && q == p) return off;
+            off += fast_ns(N, t, q);
+        }
+    return off;
+}
+MCI_HD constexpr int fast_tw_count(int N) { return fast_tw_offset(N, 2, 0); }
+
 // One size class as the kernels see it.
 struct ClassDev {
     int P;       // samples per channel
@@ -81,6 +122,8 @@ struct ClassDev {
     int chan_len;        // reals per input channel: P, or 2 P for complex signals
     int64_t in_len;      // reals per signal: M_in * chan_len
     int64_t out_len;     // reals per signal: n_out * T (x 2 for complex signals)
+    int fast;            // served by the fused radix-8 kernel (mci_fast.cu)
+    int tw_rel;          // fused path: offset (complex) of the class table after its weights
 };
 
 // Device-built grouping of one mci_interp_1d call (uneven batches).
@@ -176,6 +219,8 @@ struct KArgs {
 
 // Kernel for (precision, column pattern, FFT length), or NULL when not compiled.
 const void* kernel_lookup(int precision, bool cols, int N);
+// Fused radix-8 kernel for (N, input channels, scale, outputs), or NULL when not compiled.
+const void* fast_kernel_lookup(int N, int M_in, int s, int n_out);
 
 int launch_sched_1d(const int* size_class, int64_t batch, int n_classes, const ClassLaunch* cl,
                     const int* order, int64_t* sorted, Sched1D* st, int64_t* in_pref,

@@ -6,6 +6,45 @@
 
 namespace mci {
 
+// Signals of a contiguous-signal tile (1-D modes and image rows): their count (returned,
+// at most G) and their input and output offsets in s_in[g], s_out[g] (shared memory).
+// All threads call it; it ends with a barrier.
+__device__ __forceinline__ int tile_signal_offsets(const KArgs& a, int G, int item, int list0,
+                                                   int64_t* s_in, int64_t* s_out, int* s_cnt)
+{
+    const ClassDev& c = a.c;
+    if (threadIdx.x == 0) {
+        int cnt;
+        if (a.mode == kModeUniform) {
+            cnt = (int)min((int64_t)G, a.batch - (int64_t)item * G);
+        } else if (a.mode == kModeSorted) {
+            cnt = min(G, a.sched1->count[a.cls] - item * G);
+        } else {
+            const int2 it = a.items[list0 + item];
+            cnt = min(G, a.h[it.x] - it.y * G);
+        }
+        *s_cnt = cnt;
+    }
+    __syncthreads();
+    const int cnt = *s_cnt;
+    if (threadIdx.x < cnt) {
+        const int g = threadIdx.x;
+        if (a.mode == kModeRows) {
+            const int2 it = a.items[list0 + item];
+            const int i = it.x, r = it.y * G + g;
+            s_in[g] = a.img_in_off[i] + (int64_t)r * a.w[i];
+            s_out[g] = a.inter_off[i] + (int64_t)r * c.T;
+        } else {
+            const int64_t b = a.mode == kModeSorted ? a.sorted[a.sched1->start[a.cls] + (int64_t)item * G + g]
+                                                    : (int64_t)item * G + g;
+            s_in[g] = a.in_off ? a.in_off[b] : b * c.in_len;
+            s_out[g] = a.out_off ? a.out_off[b] : b * c.out_len;
+        }
+    }
+    __syncthreads();
+    return cnt;
+}
+
 // One tile (one work item) of a size-class launch.
 template <typename R, int N, bool COLS>
 __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list0, cpx<R>* sm)
@@ -28,36 +67,7 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
         store_cols<R>(sm, c, static_cast<R*>(a.out), a.img_out_off[i] + c0, ld, cnt);
         __syncthreads();
     } else {
-        if (threadIdx.x == 0) {
-            int cnt;
-            if (a.mode == kModeUniform) {
-                cnt = (int)min((int64_t)G, a.batch - (int64_t)item * G);
-            } else if (a.mode == kModeSorted) {
-                cnt = min(G, a.sched1->count[a.cls] - item * G);
-            } else {
-                const int2 it = a.items[list0 + item];
-                cnt = min(G, a.h[it.x] - it.y * G);
-            }
-            s_cnt = cnt;
-        }
-        __syncthreads();
-        const int cnt = s_cnt;
-        if (threadIdx.x < cnt) {
-            const int g = threadIdx.x;
-            if (a.mode == kModeRows) {
-                const int2 it = a.items[list0 + item];
-                const int i = it.x, r = it.y * G + g;
-                s_in[g] = a.img_in_off[i] + (int64_t)r * a.w[i];
-                s_out[g] = a.inter_off[i] + (int64_t)r * c.T;
-            } else {
-                const int64_t b = a.mode == kModeSorted
-                                      ? a.sorted[a.sched1->start[a.cls] + (int64_t)item * G + g]
-                                      : (int64_t)item * G + g;
-                s_in[g] = a.in_off ? a.in_off[b] : b * c.in_len;
-                s_out[g] = a.out_off ? a.out_off[b] : b * c.out_len;
-            }
-        }
-        __syncthreads();
+        const int cnt = tile_signal_offsets(a, G, item, list0, s_in, s_out, &s_cnt);
         // signals whose complex pairs are 8-byte aligned are read by the first FFT pass
         // directly; others are staged in shared memory first
         bool direct = c.cplx || (c.P % 2) == 0;

@@ -337,3 +337,44 @@ def test_upsample_2d_large_images_match_oracle(cuda_device, where):
         pos += W * W
         check(got, _oracle_columns(im, s, systems, cols), "fp32")
     plan.close()
+
+
+@pytest.mark.parametrize("P", [256, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("aligned", [True, False])
+def test_fused_radix8_classes(cuda_device, P, aligned):
+    """The batched workload's classes (M = 3 {f, Hf, f'}, T = 4P, f only, FP32) run on the
+    fused radix-8 kernel (2048 / (P/2) signals per CTA); a ragged last tile, half trig
+    polynomials and half smooth non-bandlimited signals.  Unaligned offsets take the
+    element-wise load and store branches."""
+    systems = [F, H, D1]
+    N = P // 2
+    G = 2048 // N
+    batch = 2 * G + 3
+    rng = S.rng_for(1, 40 + P)
+    g = np.concatenate([S.signal_batch_1d(rng, P, batch // 2, systems, "trig")[0],
+                        S.signal_batch_1d(rng, P, batch - batch // 2, systems, "smooth")[0]])
+    plan = mci.Plan(systems, P, 4 * P, max_batch=batch)
+    assert plan.info()["signals_per_cta"][0] == G
+    pad = 0 if aligned else 1
+    in_off = np.arange(batch, dtype=np.int64) * (3 * P + pad) + pad
+    out_off = np.arange(batch, dtype=np.int64) * (4 * P + pad) + pad
+    flat = np.zeros(int(in_off[-1]) + 3 * P + pad)
+    for b in range(batch):
+        flat[in_off[b]:in_off[b] + 3 * P] = g[b].ravel()
+    x = torch.tensor(flat, dtype=torch.float32, device="cuda")
+    y = torch.full((int(out_off[-1]) + 4 * P + pad,), float("nan"), device="cuda")
+    mci.mci_interp_1d(plan.handle, x, torch.tensor(in_off, device="cuda"), y,
+                      torch.tensor(out_off, device="cuda"), None, batch)
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    plan.close()
+    yh = y.cpu().double().numpy()
+    xs = x.cpu().double().numpy()
+    sel = np.unique(np.r_[0, 1, G - 1, G, batch // 2, batch - 2, batch - 1])
+    gs = np.stack([xs[in_off[b]:in_off[b] + 3 * P].reshape(3, P) for b in sel])
+    ref = O.mci_direct(systems, gs, 4 * P)
+    got = np.stack([yh[out_off[b]:out_off[b] + 4 * P] for b in sel])[:, None, :]
+    check(got, ref, "fp32")
+    if not aligned:   # the padding elements between signals stay untouched
+        gaps = np.concatenate([yh[out_off[b] - 1:out_off[b]] for b in range(batch)])
+        assert np.all(np.isnan(gaps))
