@@ -176,6 +176,9 @@ typedef struct {
     int smem_bytes;          /* dynamic shared memory per CTA                             */
     int64_t table_bytes;     /* device bytes of per-residue tables and twiddles           */
     int64_t workspace_bytes; /* device bytes of the 1-D and 2-D workspace                 */
+    unsigned fused_mask;     /* bit c: size class c runs on the fused radix-8 kernel      */
+    int persistent_ctas;     /* grid of the one persistent launch that serves uneven
+                                batches when every class is fused (0: one launch per class) */
 } mci_plan_stats;
 
 /*

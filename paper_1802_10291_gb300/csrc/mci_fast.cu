@@ -134,24 +134,30 @@ __device__ __forceinline__ void middle_passes(C* sm, int j, const C* tab)
     }
 }
 
+// One tile of the fused path: its signals and where their data live.
+struct FastTile {
+    const C* W;              // the class's bin weights
+    const C* tab;            // the class's fused-path table
+    const float* in;
+    float* out;
+    const int64_t* s_in;     // per signal of the tile (shared memory)
+    const int64_t* s_out;
+    int cnt;                 // signals in the tile
+};
+
+// The whole pipeline for one tile (all threads of the CTA; smem_raw holds the buffers).
 template <int N, int MIN, int S, int NOUT>
-__global__ void __launch_bounds__(256, 2) mci_fast_kernel(const KArgs a)
+__device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* smem_raw)
 {
     constexpr int Q = S * NOUT, QM = MIN > Q ? MIN : Q;
-    constexpr int TPS = N / 8, G = 256 / TPS, L = fast_passes(N), P = 2 * N, T = S * P;
+    constexpr int TPS = N / 8, L = fast_passes(N), P = 2 * N, T = S * P;
     constexpr int HALF = TPS >= 32 ? 16 : TPS / 2;   // lane distance of mirror partners
     static_assert(N >= kFastMinN && N <= kFastMaxN && (N & (N - 1)) == 0, "fused path length");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int64_t s_in[kMaxTile];
-    __shared__ int64_t s_out[kMaxTile];
-    __shared__ int s_cnt;
-    const int list0 = a.mode == kModeRows ? a.sched2->row_start[a.cls] : 0;
-    const int cnt = tile_signal_offsets(a, G, blockIdx.x, list0, s_in, s_out, &s_cnt);
     const int tid = threadIdx.x, g = tid / TPS, t = tid - g * TPS;
-    const bool active = g < cnt;
+    const bool active = g < ft.cnt;
     C* sm = reinterpret_cast<C*>(smem_raw) + g * QM * N;
-    const C* W = static_cast<const C*>(a.W);
-    const C* tab = W + a.c.tw_rel;
+    const C* W = ft.W;
+    const C* tab = ft.tab;
     // natural butterfly index, and the permuted one of the junction: within each run of
     // 2 HALF threads, the first half takes a = w HALF + i, the second half N/8 - a (N/16
     // for a = 0), so that bins k and N - k sit on lanes l and l ^ HALF
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(256, 2) mci_fast_kernel(const KArgs a)
     {
         using P0 = Pass<N, 0, false>;
         C x[MIN][8];
-        const float* src = static_cast<const float*>(a.in) + (active ? s_in[g] : 0);
+        const float* src = ft.in + (active ? ft.s_in[g] : 0);
         const bool al = (reinterpret_cast<uintptr_t>(src) & 7) == 0;
         if (active && al) {
 #pragma unroll
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(256, 2) mci_fast_kernel(const KArgs a)
         PL::template load<Q>(sm, jn, y);
         PL::template compute<Q>(y, jn, tab);
         // all lanes take part in the shuffles below; only active signals store
-        float* dst0 = static_cast<float*>(a.out) + (active ? s_out[g] : 0);
+        float* dst0 = ft.out + (active ? ft.s_out[g] : 0);
         // element l of phase buffer (o, u) holds samples s (2l) + u (real part) and
         // s (2l + 1) + u (imaginary part) of output o
         const bool al = (reinterpret_cast<uintptr_t>(dst0) & ((S % 2) == 0 ? 15 : 7)) == 0;
@@ -328,24 +334,111 @@ __global__ void __launch_bounds__(256, 2) mci_fast_kernel(const KArgs a)
     }
 }
 
+// One CTA per tile of one size class.
+template <int N, int MIN, int S, int NOUT>
+__global__ void __launch_bounds__(256, 2) mci_fast_kernel(const KArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int64_t s_in[kMaxTile];
+    __shared__ int64_t s_out[kMaxTile];
+    __shared__ int s_cnt;
+    const int list0 = a.mode == kModeRows ? a.sched2->row_start[a.cls] : 0;
+    const int cnt = tile_signal_offsets(a, 2048 / N, blockIdx.x, list0, s_in, s_out, &s_cnt);
+    const C* W = static_cast<const C*>(a.W);
+    fast_tile<N, MIN, S, NOUT>(FastTile{W, W + a.c.tw_rel, static_cast<const float*>(a.in),
+                                        static_cast<float*>(a.out), s_in, s_out, cnt},
+                               smem_raw);
+}
+
 }  // namespace
 
 #define MCI_FAST_VARIANTS(X) \
-    X(128, 3, 4, 1) X(256, 3, 4, 1) X(512, 3, 4, 1) X(1024, 3, 4, 1) X(2048, 3, 4, 1)
+    X(0, 128, 3, 4, 1) X(1, 256, 3, 4, 1) X(2, 512, 3, 4, 1) X(3, 1024, 3, 4, 1) X(4, 2048, 3, 4, 1)
 
-const void* fast_kernel_lookup(int N, int M_in, int s, int n_out)
+namespace {
+
+// Tile `item` of the persistent launch: class order[oi] (its tiles start at s_t0[oi]),
+// signals sorted[start + (item - s_t0[oi]) G ..]; their offsets and count go to shared memory
+// (every thread stores the same oi and count).
+__device__ __forceinline__ void persistent_item_signals(const PersistArgs& pa, const int* s_t0, int item,
+                                                        int* oi_out, int64_t* s_in, int64_t* s_out, int* cnt)
 {
-#define MCI_FAST_CASE(n, m, sc, no) \
-    if (N == n && M_in == m && s == sc && n_out == no) return (const void*)mci_fast_kernel<n, m, sc, no>;
+    int oi = 0;
+    while (oi + 1 < pa.n_classes && item >= s_t0[oi + 1]) ++oi;
+    const int c = pa.order[oi];
+    const ClassDev& cd = pa.cl[c].c;
+    const int tile = item - s_t0[oi];
+    const int n = min(cd.G, pa.sched->count[c] - tile * cd.G);
+    *oi_out = oi;
+    if (threadIdx.x < n) {
+        const int64_t b = pa.sorted[pa.sched->start[c] + (int64_t)tile * cd.G + threadIdx.x];
+        s_in[threadIdx.x] = pa.in_off ? pa.in_off[b] : b * cd.in_len;
+        s_out[threadIdx.x] = pa.out_off ? pa.out_off[b] : b * cd.out_len;
+    }
+    *cnt = n;
+}
+
+// Persistent launch over all fused classes of an uneven batch.  The tiles are numbered class
+// after class, largest P first (the small tiles fill the tail); the CTAs take them from the
+// counter sched->next_tile, each claiming its next tile while it works on the current one.
+__global__ void __launch_bounds__(256, 2) mci_fast_persistent(const PersistArgs pa)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int64_t s_in[kMaxTile];
+    __shared__ int64_t s_out[kMaxTile];
+    __shared__ int s_t0[MCI_MAX_SIZES + 1];
+    __shared__ int s_cnt, s_oi, s_item;
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int oi = 0; oi < pa.n_classes; ++oi) {
+            s_t0[oi] = t;
+            const int c = pa.order[oi];
+            t += (pa.sched->count[c] + pa.cl[c].c.G - 1) / pa.cl[c].c.G;
+        }
+        s_t0[pa.n_classes] = t;
+        s_item = (int)atomicAdd(&pa.sched->next_tile, 1u);
+    }
+    __syncthreads();
+    const int total = s_t0[pa.n_classes];
+    while (s_item < total) {
+        persistent_item_signals(pa, s_t0, s_item, &s_oi, s_in, s_out, &s_cnt);
+        __syncthreads();
+        unsigned next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(&pa.sched->next_tile, 1u);   // in flight meanwhile
+        const ClassLaunch& L = pa.cl[pa.order[s_oi]];
+        const C* W = static_cast<const C*>(L.W);
+        const FastTile ft{W, W + L.c.tw_rel, pa.in, pa.out, s_in, s_out, s_cnt};
+        switch (L.c.fast - 1) {
+#define MCI_FAST_PCASE(v, n, m, sc, no) \
+    case v: fast_tile<n, m, sc, no>(ft, smem_raw); break;
+            MCI_FAST_VARIANTS(MCI_FAST_PCASE)
+#undef MCI_FAST_PCASE
+        }
+        if (threadIdx.x == 0) s_item = (int)next;
+        __syncthreads();   // buffers and the tile's offsets are free again; s_item is the next tile
+    }
+}
+
+}  // namespace
+
+const void* fast_kernel_lookup(int N, int M_in, int s, int n_out, int* variant)
+{
+#define MCI_FAST_CASE(v, n, m, sc, no)                              \
+    if (N == n && M_in == m && s == sc && n_out == no) {             \
+        if (variant) *variant = v;                                   \
+        return (const void*)mci_fast_kernel<n, m, sc, no>;           \
+    }
     MCI_FAST_VARIANTS(MCI_FAST_CASE)
 #undef MCI_FAST_CASE
     return nullptr;
 }
 
+const void* fast_persistent_kernel() { return (const void*)mci_fast_persistent; }
+
 // Device-side launch of a fused-path class (dynamic parallelism, from the scheduler).
 __device__ bool device_launch_fast(const ClassDev& c, int grid, int smem, const KArgs& a)
 {
-#define MCI_FAST_DCASE(n, m, sc, no)                                                          \
+#define MCI_FAST_DCASE(v, n, m, sc, no)                                                       \
     if (c.N == n && c.M_in == m && c.s == sc && c.n_out == no) {                               \
         mci_fast_kernel<n, m, sc, no><<<grid, 256, smem, cudaStreamFireAndForget>>>(a);        \
         return true;                                                                          \

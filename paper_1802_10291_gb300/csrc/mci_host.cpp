@@ -244,6 +244,9 @@ struct mci_plan_s {
     std::vector<const void*> kern;    // per class host kernel (contiguous pattern)
     std::vector<const void*> kern_cols;
     std::vector<int> csmem;           // per class dynamic shared memory
+    int persist = 0;                  // uneven batches: one persistent launch (all classes fused)
+    int persist_ctas = 0;             // its grid: resident CTAs per SM x SMs
+    int persist_smem = 0;
     int n_out = 0;
     int M_in = 0;
     int smem = 0;                     // largest per-class shared memory
@@ -551,6 +554,30 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
 
 }  // namespace
 
+// One persistent launch over the grouped batch (sorted, st in device memory; st->next_tile is
+// zero when it starts).  tiles < 0: not known on the host (grouped on the device).
+static cudaError_t launch_persistent(mci_plan_t p, const KArgs& a, const int64_t* sorted, Sched1D* st,
+                                     const int64_t* in_off, const int64_t* out_off, int64_t tiles,
+                                     cudaStream_t s)
+{
+    PersistArgs pa{};
+    pa.cl = p->d_launch;
+    pa.order = p->d_order;
+    pa.n_classes = (int)p->cls.size();
+    pa.sched = st;
+    pa.sorted = sorted;
+    pa.in = static_cast<const float*>(a.in);
+    pa.out = static_cast<float*>(a.out);
+    pa.in_off = in_off;
+    pa.out_off = out_off;
+    int64_t grid = p->persist_ctas;
+    if (tiles >= 0) grid = std::min(grid, tiles);
+    if (grid <= 0) return cudaSuccess;
+    void* args[] = {&pa};
+    return cudaLaunchKernel(fast_persistent_kernel(), dim3((unsigned)grid), dim3(kThreads), args,
+                            (size_t)p->persist_smem, s);
+}
+
 // Uneven batch whose size classes are in host memory: stable grouping on the host
 // into a pinned staging block (two blocks alternate; a block is reused only after
 // its previous upload has completed), one upload, then every non-empty class is
@@ -590,12 +617,19 @@ static mci_status interp_1d_host_grouped(mci_plan_t p, KArgs a, const int* size_
         pin += p->cdev[c].in_len;
         pout += p->cdev[c].out_len;
     }
+    st->next_tile = 0;
     cudaError_t e = cudaMemcpyAsync(p->d_sorted, blk, p->stage_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev, s);
     p->stage_cur ^= 1;
     if (!a.in_off) a.in_off = p->d_in_pref;
     if (!a.out_off) a.out_off = p->d_out_pref;
     a.mode = kModeSorted;
+    if (p->persist) {
+        int64_t tiles = 0;
+        for (int c = 0; c < n; ++c) tiles += (cnt[c] + p->cdev[c].G - 1) / p->cdev[c].G;
+        if (e == cudaSuccess) e = launch_persistent(p, a, p->d_sorted, p->d_sched1, a.in_off, a.out_off, tiles, s);
+        return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
+    }
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
     for (int oi = 0; oi < n && e == cudaSuccess; ++oi) {
         const int c = p->order[oi];
@@ -965,9 +999,12 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         cd_.out_len = (int64_t)cd_.n_out * hc.T * (d.complex_signal ? 2 : 1);
         // fused radix-8 kernel: real FP32 1-D classes with N a power of two in its range and a
         // compiled (channels, scale, outputs) variant; its tile and shared memory are fixed
+        int var = -1;
         cd_.fast = d.precision == MCI_FP32 && !d.complex_signal && d.max_images == 0 &&
-                   hc.N >= kFastMinN && hc.N <= kFastMaxN && (hc.N & (hc.N - 1)) == 0 &&
-                   fast_kernel_lookup(hc.N, cd_.M_in, hc.s, p->n_out) != nullptr;
+                           hc.N >= kFastMinN && hc.N <= kFastMaxN && (hc.N & (hc.N - 1)) == 0 &&
+                           fast_kernel_lookup(hc.N, cd_.M_in, hc.s, p->n_out, &var) != nullptr
+                       ? 1 + var
+                       : 0;
         if (cd_.fast) continue;
         const int per = cd_.sstride * csz + smem_twiddle_count(hc.N) * csz;
         if (per > smem_cap) {
@@ -1062,6 +1099,29 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             }
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
         }
+    }
+    // uneven batches whose classes are all on the fused path: one persistent launch
+    p->persist = n > 1 && fast_persistent_kernel() != nullptr;
+    for (int c = 0; c < n; ++c) {
+        p->persist = p->persist && p->cdev[c].fast;
+        p->persist_smem = std::max(p->persist_smem, p->csmem[c]);
+    }
+    if (e == cudaSuccess && p->persist) {
+        const void* k = fast_persistent_kernel();
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, k);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, p->persist_smem);
+        const int need = 2 * (p->persist_smem + (int)fa.sharedSizeBytes + 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     std::min(100, (100 * need + (int)prop.sharedMemPerMultiprocessor - 1) /
+                                                       (int)prop.sharedMemPerMultiprocessor));
+        int per_sm = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, kThreads, p->persist_smem);
+        p->persist_ctas = per_sm * prop.multiProcessorCount;
+        if (e == cudaSuccess && p->persist_ctas <= 0) p->persist = 0;
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_launch, p->launch.data(), sizeof(ClassLaunch) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_order, p->order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
@@ -1238,7 +1298,10 @@ mci_status mci_interp_1d(mci_plan_t p, const void* in, const int64_t* in_off, vo
         if (!on_device) return interp_1d_host_grouped(p, a, size_class, batch, s);
         e = (cudaError_t)launch_sched_1d(size_class, batch, n, p->d_launch, p->d_order, p->d_sorted,
                                          p->d_sched1, in_off ? nullptr : p->d_in_pref,
-                                         out_off ? nullptr : p->d_out_pref, a, s);
+                                         out_off ? nullptr : p->d_out_pref, a, s, p->persist);
+        if (e == cudaSuccess && p->persist)
+            e = launch_persistent(p, a, p->d_sorted, p->d_sched1, in_off ? in_off : p->d_in_pref,
+                                  out_off ? out_off : p->d_out_pref, -1, s);
     }
     return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
 }
@@ -1329,6 +1392,9 @@ mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)
     st->smem_bytes = p->smem;
     st->table_bytes = p->table_bytes;
     st->workspace_bytes = p->work_bytes;
+    for (size_t c = 0; c < p->cdev.size(); ++c)
+        if (p->cdev[c].fast) st->fused_mask |= 1u << c;
+    st->persistent_ctas = p->persist ? p->persist_ctas : 0;
     cudaError_t e = cudaStreamSynchronize(p->last_stream);
     int status = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
@@ -1496,7 +1562,11 @@ mci_status mci_interp_1d_noalloc(mci_plan_t p, const void* in, const int64_t* in
         e = (cudaError_t)launch_sched_1d(size_class, batch, n, p->d_launch, p->d_order,
                                          noalloc_sorted(scratch), noalloc_sched(scratch),
                                          in_off ? nullptr : noalloc_in_pref(scratch),
-                                         out_off ? nullptr : noalloc_out_pref(scratch), a, s);
+                                         out_off ? nullptr : noalloc_out_pref(scratch), a, s, p->persist);
+        if (e == cudaSuccess && p->persist)
+            e = launch_persistent(p, a, noalloc_sorted(scratch), noalloc_sched(scratch),
+                                  in_off ? in_off : noalloc_in_pref(scratch),
+                                  out_off ? out_off : noalloc_out_pref(scratch), -1, s);
     }
     return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
 }

@@ -122,14 +122,15 @@ struct ClassDev {
     int chan_len;        // reals per input channel: P, or 2 P for complex signals
     int64_t in_len;      // reals per signal: M_in * chan_len
     int64_t out_len;     // reals per signal: n_out * T (x 2 for complex signals)
-    int fast;            // served by the fused radix-8 kernel (mci_fast.cu)
+    int fast;            // fused radix-8 kernel (mci_fast.cu): 1 + its variant index, or 0
     int tw_rel;          // fused path: offset (complex) of the class table after its weights
 };
 
-// Device-built grouping of one mci_interp_1d call (uneven batches).
+// Grouping of one mci_interp_1d call (uneven batches), built on the device or on the host.
 struct Sched1D {
     int start[MCI_MAX_SIZES];          // first position of each class in the sorted list
     int count[MCI_MAX_SIZES];          // signals per class
+    unsigned next_tile;                // work counter of the persistent launch (zero per call)
 };
 
 // What the device-side scheduler needs to launch one size class.
@@ -219,12 +220,29 @@ struct KArgs {
 
 // Kernel for (precision, column pattern, FFT length), or NULL when not compiled.
 const void* kernel_lookup(int precision, bool cols, int N);
-// Fused radix-8 kernel for (N, input channels, scale, outputs), or NULL when not compiled.
-const void* fast_kernel_lookup(int N, int M_in, int s, int n_out);
+// Fused radix-8 kernel for (N, input channels, scale, outputs), or NULL when not compiled;
+// *variant (if not NULL) receives its index in the persistent kernel's dispatch.
+const void* fast_kernel_lookup(int N, int M_in, int s, int n_out, int* variant = nullptr);
+
+// One persistent launch over an uneven batch whose classes are all on the fused path: the
+// CTAs take tiles from sched->next_tile (zero at launch), classes in `order` (largest P
+// first), the signals of class c at sorted[start[c] ..], offsets in_off / out_off.
+struct PersistArgs {
+    const ClassLaunch* cl;
+    const int* order;
+    int n_classes;
+    Sched1D* sched;
+    const int64_t* sorted;
+    const float* in;
+    float* out;
+    const int64_t* in_off;
+    const int64_t* out_off;
+};
+const void* fast_persistent_kernel();
 
 int launch_sched_1d(const int* size_class, int64_t batch, int n_classes, const ClassLaunch* cl,
                     const int* order, int64_t* sorted, Sched1D* st, int64_t* in_pref,
-                    int64_t* out_pref, const KArgs& tmpl, void* stream);
+                    int64_t* out_pref, const KArgs& tmpl, void* stream, int persist);
 int launch_sched_2d(int64_t n_img, int n_classes, const ClassLaunch* cl, int64_t max_inter,
                     int64_t max_items, int64_t* inter_off, int64_t* lr_pref, int64_t* hr_pref,
                     int* row_cls, int* col_cls, int2* items, Sched2D* st, const KArgs& rows_tmpl,

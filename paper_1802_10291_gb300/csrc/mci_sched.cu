@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kSchedThreads)
 sched_1d_kernel(const int* __restrict__ size_class, int64_t batch, int n_classes,
                 const ClassLaunch* __restrict__ cl, const int* __restrict__ order,
                 int64_t* __restrict__ sorted, Sched1D* __restrict__ st, int64_t* in_pref,
-                int64_t* out_pref, KArgs tmpl)
+                int64_t* out_pref, KArgs tmpl, int persist)
 {
     __shared__ int cnt[MCI_MAX_SIZES], cursor[MCI_MAX_SIZES], start[MCI_MAX_SIZES];
     if (threadIdx.x < MCI_MAX_SIZES) {
@@ -118,6 +118,10 @@ sched_1d_kernel(const int* __restrict__ size_class, int64_t batch, int n_classes
     }
     __threadfence();
     __syncthreads();
+    if (persist) {   // the host launches the persistent kernel next, stream-ordered
+        if (threadIdx.x == 0) st->next_tile = 0;
+        return;
+    }
     if (threadIdx.x == 0) {
         for (int oi = 0; oi < n_classes; ++oi) {
             const int c = order[oi];
@@ -136,10 +140,10 @@ sched_1d_kernel(const int* __restrict__ size_class, int64_t batch, int n_classes
 
 int launch_sched_1d(const int* size_class, int64_t batch, int n_classes, const ClassLaunch* cl,
                     const int* order, int64_t* sorted, Sched1D* st, int64_t* in_pref,
-                    int64_t* out_pref, const KArgs& tmpl, void* stream)
+                    int64_t* out_pref, const KArgs& tmpl, void* stream, int persist)
 {
     sched_1d_kernel<<<1, kSchedThreads, 0, (cudaStream_t)stream>>>(
-        size_class, batch, n_classes, cl, order, sorted, st, in_pref, out_pref, tmpl);
+        size_class, batch, n_classes, cl, order, sorted, st, in_pref, out_pref, tmpl, persist);
     return (int)cudaGetLastError();
 }
 
