@@ -41,10 +41,12 @@ WORKLOAD = ("batched 1-D MCI: 16384 signals, M=3 {identity, Hilbert -i sgn, deri
 # same sample gives the realised FP32/FP64 errors.
 CPU_PER_CLASS = 100
 
-# DRAM bytes (read + write) per signal of the timed roofline kernel (the fused radix-8
-# kernel of the P = 4096 class, M = 3, T = 16384), from one ncu capture of that launch.
+# DRAM bytes (read + write) of one launch of the roofline kernel (the persistent launch that
+# serves the whole batched step), from one ncu capture of that launch on this workload.
 # None whenever the kernel has changed since the capture.
-ROOFLINE_TRAFFIC_PER_SIGNAL = None
+ROOFLINE_TRAFFIC_PER_STEP = None
+# the same for the P = 4096 class kernel timed alone (3201 signals), per signal
+CLASS4096_TRAFFIC_PER_SIGNAL = (157665024 + 153586688) / 3201
 
 
 def peaks():
@@ -867,21 +869,28 @@ def main():
                              % (4 * batch["n_in"] / 1e6, 4 * batch["n_out"] / 1e6),
                        "parallelism": f"independent signals per GPU x{world}"},
             "clocks": clocks,
-            "gpu_launches": n_cls * args.steps,
-            "roofline": {"bound": "hbm", "achieved": k_achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": k_achieved / hbm,
-                         "traffic": (None if ROOFLINE_TRAFFIC_PER_SIGNAL is None
-                                     else ROOFLINE_TRAFFIC_PER_SIGNAL * sel.size),
-                         "kernel": ("mci_fast_kernel<2048, 3, 4, 1>" if plan4.info()["signals_per_cta"][0] == 1
-                                    and plan4.info()["smem_bytes"] == 65536 else "mci_kernel<float, 2048>")
-                                   + " (P=4096 class, 3201 signals), timed alone",
-                         "bytes_per_launch": k_bytes, "ms_per_launch": k_ms,
-                         "peak_source": f"{peak_kind} hbm_gbs"},
+            # one persistent launch per step when every class is fused, else one per class
+            "gpu_launches": (1 if info["persistent_ctas"] > 0 else n_cls) * args.steps,
+            # the step is one persistent launch: its duration is taken as the step time of the
+            # CUDA events (which also hold the upload of the host grouping, ~0.4 MB), so
+            # `achieved` is a lower bound for the kernel
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": ROOFLINE_TRAFFIC_PER_STEP,
+                         "kernel": ("mci_fast_persistent (all five classes, one launch per step)"
+                                    if info["persistent_ctas"] > 0 else "per-class kernels"),
+                         "bytes_per_launch": bytes_step, "ms_per_launch": 1e3 * secs / args.steps,
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "class_kernel_4096": {
+                             "kernel": ("mci_fast_kernel<2048, 3, 4, 1>" if plan4.info()["fused_mask"] & 1
+                                        else "mci_kernel<float, 2048>") + " (P=4096 class, 3201 signals), timed alone",
+                             "bytes_per_launch": k_bytes, "ms_per_launch": k_ms, "achieved": k_achieved,
+                             "frac": k_achieved / hbm,
+                             "traffic": CLASS4096_TRAFFIC_PER_SIGNAL * sel.size}},
             "step_roofline": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                               "bytes_per_step": bytes_step},
             "device_grouped": {"ms_per_step": ms_dev, "value": out_samples / (ms_dev / 1e3) / 1e6,
                                "unit": UNIT, "note": "size classes in device memory: grouping "
-                               "and per-class launches on the device",
+                               "kernel, then the persistent launch (two launches, no host work)",
                                "cuda_graph_ms_per_step": ms_graph},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * secs64 / steps64,
                      "speedup_fp32_over_fp64": value / value64},
@@ -904,7 +913,8 @@ def main():
                            "ms_per_step": 1e3 * secs_st / e2e_steps,
                            "mode": "staged: copies in, compute, copies out pipelined in 16 MB chunks"},
             "cpu_baseline": cpu,
-            "plan": {"smem_bytes": info["smem_bytes"], "signals_per_cta": info["signals_per_cta"][:n_cls]},
+            "plan": {"smem_bytes": info["smem_bytes"], "signals_per_cta": info["signals_per_cta"][:n_cls],
+                     "fused_mask": info["fused_mask"], "persistent_ctas": info["persistent_ctas"]},
         }
         print(json.dumps(line), flush=True)
     if world > 1:
