@@ -244,6 +244,7 @@ struct mci_plan_s {
     std::vector<const void*> kern;    // per class host kernel (contiguous pattern)
     std::vector<const void*> kern_cols;
     std::vector<int> csmem;           // per class dynamic shared memory
+    int n_sm = 0;                     // multiprocessors of the plan's device
     int persist = 0;                  // uneven batches: one persistent launch (all classes fused)
     int persist_ctas = 0;             // its grid: resident CTAs per SM x SMs
     int persist_smem = 0;
@@ -967,6 +968,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         return MCI_ERR_CUDA;
     }
     const int smem_cap = (int)prop.sharedMemPerBlockOptin - 2048;  // static shared memory margin
+    p->n_sm = prop.multiProcessorCount;
     const int csz = (int)(2 * p->elem);
     int need = 0;
     int Pmax = 0, Tmax = 0;
@@ -1285,8 +1287,15 @@ mci_status mci_interp_1d(mci_plan_t p, const void* in, const int64_t* in_off, vo
         const int64_t items = (batch + p->cdev[0].G - 1) / p->cdev[0].G;
         if (items > 0x7fffffff) return MCI_ERR_UNSUPPORTED_SIZE;
         a.uniform_items = (int)items;
+        // few tiles with many output phases (e.g. one short signal evaluated on a long grid):
+        // spread each tile's phases over several CTAs (at least 8 phases each)
+        const ClassDev& c0 = p->cdev[0];
+        int qch = 1;
+        if (!c0.fast && !c0.cplx && c0.Q >= 16 && items < p->n_sm)
+            qch = (int)std::max<int64_t>(1, std::min<int64_t>(c0.Q / 8, 2 * p->n_sm / items));
+        a.qchunks = qch;
         void* args[] = {&a};
-        e = cudaLaunchKernel(p->kern[0], dim3((unsigned)items), dim3(kThreads), args,
+        e = cudaLaunchKernel(p->kern[0], dim3((unsigned)items, (unsigned)qch), dim3(kThreads), args,
                              (size_t)p->csmem[0], s);
     } else {
         cudaPointerAttributes attr{};

@@ -204,6 +204,7 @@ struct KArgs {
     const int64_t* out_off;
     int64_t batch;
     int uniform_items;
+    int qchunks;             // > 1: the phases of every tile are spread over gridDim.y CTAs
     const int64_t* sorted;   // signals sorted by class
     const Sched1D* sched1;
     // 2-D

@@ -74,15 +74,22 @@ __device__ __forceinline__ void mci_tile_item(const KArgs& a, int item, int list
         for (int g = 0; g < cnt; ++g)
             direct = direct && ((reinterpret_cast<uintptr_t>(static_cast<const R*>(a.in) + s_in[g]) &
                                  (2 * sizeof(R) - 1)) == 0);
+        // phases of this CTA: all, or the blockIdx.y-th of qchunks shares (real signals)
+        int q0 = 0, q1 = c.Q;
+        if (a.qchunks > 1 && !c.cplx) {
+            const int per = (c.Q + a.qchunks - 1) / a.qchunks;
+            q0 = min(c.Q, (int)blockIdx.y * per);
+            q1 = min(c.Q, q0 + per);
+        }
         if (direct) {
-            compute_tile<R, N>(sm, c, cnt, W, static_cast<const R*>(a.in), s_in);
+            compute_tile<R, N>(sm, c, cnt, W, static_cast<const R*>(a.in), s_in, q0, q1);
         } else {
             load_contig<R>(sm, c, static_cast<const R*>(a.in), s_in, cnt);
             __syncthreads();
-            compute_tile<R, N>(sm, c, cnt, W);
+            compute_tile<R, N>(sm, c, cnt, W, nullptr, nullptr, q0, q1);
         }
         if (c.cplx) store_contig_complex<R, N>(sm, c, static_cast<R*>(a.out), s_out, cnt);
-        else store_contig<R, N>(sm, c, static_cast<R*>(a.out), s_out, cnt);
+        else store_contig<R, N>(sm, c, static_cast<R*>(a.out), s_out, cnt, q0, q1);
         __syncthreads();
     }
 }

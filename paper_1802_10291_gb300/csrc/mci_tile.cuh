@@ -39,9 +39,14 @@ __device__ __forceinline__ cpx<double> ldw(const cpx<double>* p)
     return {v.x, v.y};
 }
 
-template <typename R, int MIN, int QC>
+// SPLIT (runtime counts only): the caller spreads the phases of one pair over several
+// threads, each with phases q0 .. q1 - 1; since phase buffer q shares its storage with
+// channel buffer q, all threads read their channels, then a barrier, then write (every
+// thread of the CTA calls it once; threads with act = false only take the barrier).
+template <typename R, int MIN, int QC, bool SPLIT = false>
 __device__ __forceinline__ void combine_pair(cpx<R>* base, const ClassDev& c, int k,
-                                             const cpx<R>* __restrict__ W, cpx<R> w)
+                                             const cpx<R>* __restrict__ W, cpx<R> w, int q0 = 0,
+                                             int q1 = 1 << 30, bool act = true)
 {
     const int npad = c.npad, N = c.N, NH = N / 2;
     const int Min = MIN > 0 ? MIN : c.M_in, Q = MIN > 0 ? QC : c.Q;
@@ -106,8 +111,9 @@ __device__ __forceinline__ void combine_pair(cpx<R>* base, const ClassDev& c, in
         cpx<R> Xa[MCI_MAX_CHANNELS], Xb[MCI_MAX_CHANNELS];
 #pragma unroll
         for (int m = 0; m < MCI_MAX_CHANNELS; ++m)
-            if (m < Min) spectrum(m, Xa[m], Xb[m]);
-        for (int q = 0; q < Q; ++q) {
+            if (act && m < Min) spectrum(m, Xa[m], Xb[m]);
+        if constexpr (SPLIT) __syncthreads();
+        for (int q = q0; act && q < min(Q, q1); ++q) {   // runtime counts: phases q0 .. q1 - 1
             cpx<R> ya = mk<R>(0, 0), yb = mk<R>(0, 0);
 #pragma unroll
             for (int m = 0; m < MCI_MAX_CHANNELS; ++m) {
@@ -123,7 +129,7 @@ __device__ __forceinline__ void combine_pair(cpx<R>* base, const ClassDev& c, in
 
 template <typename R, int MIN, int QC>
 __device__ __forceinline__ void combine_loop(cpx<R>* sm, const ClassDev& c, int gcount,
-                                             const cpx<R>* __restrict__ W)
+                                             const cpx<R>* __restrict__ W, int q0 = 0, int q1 = 1 << 30)
 {
     const int total = (c.N / 2 + 1) * gcount;
     const R two_over_p = R(2) / R(c.P);
@@ -135,7 +141,7 @@ __device__ __forceinline__ void combine_loop(cpx<R>* sm, const ClassDev& c, int 
     int k = it0 / gcount, g = it0 - k * gcount;
     for (int it = it0; it < total; it += step) {
         const cpx<R> w = cis_neg_pi<R>(R(k) * two_over_p);  // e^{-2 pi i k / P}
-        combine_pair<R, MIN, QC>(sm + g * sst, c, k, W, w);
+        combine_pair<R, MIN, QC>(sm + g * sst, c, k, W, w, q0, q1);
         k += dk;
         g += dg;
         if (g >= gcount) {
@@ -145,17 +151,42 @@ __device__ __forceinline__ void combine_loop(cpx<R>* sm, const ClassDev& c, int 
     }
 }
 
+// Runtime channel/phase counts when the bin pairs of the tile cannot fill the CTA (a few
+// short signals with many output phases, e.g. P = 64 evaluated at T = 4096): items are
+// (bin pair, signal, chunk of phases), so the phases of one pair spread over threads.
+template <typename R>
+__device__ __forceinline__ void combine_loop_split(cpx<R>* sm, const ClassDev& c, int gcount,
+                                                   const cpx<R>* __restrict__ W, int qa = 0, int qb = 1 << 30)
+{
+    qb = min(qb, c.Q);                          // phases qa .. qb - 1
+    const int units = (c.N / 2 + 1) * gcount;   // at most blockDim.x / 2 (the caller's test)
+    const int chunks = max(1, min(qb - qa, (int)blockDim.x / units));
+    const int per = (qb - qa + chunks - 1) / chunks;
+    const int it = ltid();                         // one item per thread at most
+    const bool act = it < units * chunks;
+    const int u = act ? it / chunks : 0, ch = act ? it - u * chunks : 0;
+    const int k = u / gcount, g = u - k * gcount;
+    const cpx<R> w = cis_neg_pi<R>(R(k) * (R(2) / R(c.P)));  // e^{-2 pi i k / P}
+    combine_pair<R, 0, 0, true>(sm + g * c.sstride, c, k, W, w, qa + ch * per, min(qb, qa + (ch + 1) * per), act);
+}
+
 // Channel/phase counts with a compile-time combine: M = 3 measured channels with
 // s = 4 phases (batched 1-D), and one channel with s = 2, 3, 4 (image rows and
 // columns with derivative channels formed from the samples).
 template <typename R>
 __device__ __forceinline__ void combine_tile(cpx<R>* sm, const ClassDev& c, int gcount,
-                                             const cpx<R>* __restrict__ W)
+                                             const cpx<R>* __restrict__ W, int q0 = 0, int q1 = 1 << 30)
 {
+    if (q0 > 0 || q1 < c.Q) {   // this CTA's share of the phases (runtime counts)
+        if (2 * (c.N / 2 + 1) * gcount <= (int)blockDim.x) combine_loop_split<R>(sm, c, gcount, W, q0, q1);
+        else combine_loop<R, 0, 0>(sm, c, gcount, W, q0, q1);
+        return;
+    }
     if (c.M_in == 3 && c.Q == 4) combine_loop<R, 3, 4>(sm, c, gcount, W);
     else if (c.M_in == 1 && c.Q == 2) combine_loop<R, 1, 2>(sm, c, gcount, W);
     else if (c.M_in == 1 && c.Q == 3) combine_loop<R, 1, 3>(sm, c, gcount, W);
     else if (c.M_in == 1 && c.Q == 4) combine_loop<R, 1, 4>(sm, c, gcount, W);
+    else if (c.Q > 4 && 2 * (c.N / 2 + 1) * gcount <= (int)blockDim.x) combine_loop_split<R>(sm, c, gcount, W);
     else combine_loop<R, 0, 0>(sm, c, gcount, W);
 }
 
@@ -226,10 +257,13 @@ struct SrcContig {
 // The FFT twiddles live after the tile's buffers (smem_twiddle_offset); they are
 // filled here, before or during the first pass, which needs none and ends with a barrier.
 template <typename R, int N>
+// q0, q1: a CTA that serves only phases q0 .. q1 - 1 of its signals (real signals with many
+// output phases, spread over several CTAs); by default all of them.
 __device__ __forceinline__ void compute_tile(cpx<R>* sm, const ClassDev& c, int gcount,
                                              const cpx<R>* __restrict__ W, const R* gin = nullptr,
-                                             const int64_t* s_in = nullptr)
+                                             const int64_t* s_in = nullptr, int q0 = 0, int q1 = 1 << 30)
 {
+    q1 = min(q1, c.Q);
     cpx<R>* stw = sm + c.G * c.sstride;
     auto fill = [stw] { fill_twiddles_ct<R, N, elems_per_thread(N), 1>(stw); };
     if (gin) {
@@ -241,8 +275,13 @@ __device__ __forceinline__ void compute_tile(cpx<R>* sm, const ClassDev& c, int 
         fft_many_ct<R, N, false>(sm, gcount * c.M_in, SlotBase{c.M_in, c.sstride, c.npad, c.mag_min}, stw);
     }
     if (c.cplx) combine_complex<R>(sm, c, gcount, W);
-    else combine_tile<R>(sm, c, gcount, W);
+    else combine_tile<R>(sm, c, gcount, W, q0, q1);
     __syncthreads();
+    if (q0 > 0 || q1 < c.Q) {   // inverse transforms of phases q0 .. q1 - 1 only
+        const int nq = q1 - q0;
+        fft_many_ct<R, N, true>(sm + q0 * c.npad, gcount * nq, SlotBase{nq, c.sstride, c.npad, fastdiv_magic(nq)}, stw);
+        return;
+    }
     fft_many_ct<R, N, true>(sm, gcount * c.Q, SlotBase{c.Q, c.sstride, c.npad, c.mag_q}, stw);
 }
 
@@ -301,8 +340,23 @@ __device__ __forceinline__ void load_contig(cpx<R>* sm, const ClassDev& c, const
 // FP32 with s even, else as scalars.
 template <typename R, int N>
 __device__ __forceinline__ void store_contig(const cpx<R>* sm, const ClassDev& c, R* __restrict__ out,
-                                             const int64_t* off, int gcount)
+                                             const int64_t* off, int gcount, int q0 = 0, int q1 = 1 << 30)
 {
+    q1 = min(q1, c.Q);
+    if (q0 > 0 || q1 < c.Q) {
+        // phases q0 .. q1 - 1 only: phase q = o s + u, element l -> samples s (2l) + u, s (2l + 1) + u
+        const int nq = q1 - q0, total = gcount * nq * N;
+        for (int t = ltid(); t < total; t += blockDim.x) {
+            const int gq = t / N, l = t - gq * N;
+            const int g = gq / nq, q = q0 + (gq - g * nq);
+            const int o = q / c.s, u = q - o * c.s;
+            const cpx<R> z = sm[g * c.sstride + q * c.npad + pad16(l)];
+            R* dst = out + off[g] + (int64_t)o * c.T;
+            dst[(int64_t)2 * l * c.s + u] = z.x;
+            dst[(int64_t)(2 * l + 1) * c.s + u] = z.y;
+        }
+        return;
+    }
     const int T = c.T, s = c.s, npad = c.npad, sst = c.sstride, nout = c.n_out;
     constexpr int VR = 16 / sizeof(R);     // reals per 16-byte vector
     bool vec = (s % VR) == 0 && (T % VR) == 0, vec2 = sizeof(R) == 4 && (s % 2) == 0;

@@ -378,3 +378,16 @@ def test_fused_radix8_classes(cuda_device, P, aligned):
     if not aligned:   # the padding elements between signals stay untouched
         gaps = np.concatenate([yh[out_off[b] - 1:out_off[b]] for b in range(batch)])
         assert np.all(np.isnan(gaps))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("systems,P,s,batch", [([F, D1], 64, 64, 1), ([F, H, D1], 32, 32, 3),
+                                               ([F], 128, 16, 2), ([F, D2], 48, 24, 1)],
+                         ids=lambda v: str(v))
+def test_few_signals_many_phases(cuda_device, prec, systems, P, s, batch):
+    """A few short signals on a long output grid: the s n_out phases of each tile are spread
+    over several CTAs; f, Hf and f' against the oracle."""
+    outs = ("f", "hilbert", "deriv")
+    g = S.rng_for(1, 50 + P + s).standard_normal((batch, len(systems), P))
+    out = run_1d(g, systems, s * P, prec, outputs=outs)
+    check(out, O.mci_direct(systems, g, s * P, outputs=outs), prec)
