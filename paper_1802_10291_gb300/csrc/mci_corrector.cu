@@ -15,8 +15,10 @@
 //   conv_bwd_data gin[ci] = (sum_co sum_taps w[co][ci][t] g[co](p - d_t)) * (h[ci](p) > 0),
 //                 h the ReLU output of the layer below (the same kernel with the weights
 //                 transposed, the taps reversed and an output mask);
-//   conv_bwd_w    gw[co][ci][t] = sum_p g[co](p) x[ci](p + d_t), gb[co] = sum_p g[co](p),
-//                 register-blocked sums of persistent CTAs reduced with atomics;
+//   conv_bwd_w    gw[co][ci][t] = sum_p g[co](p) x[ci](p + d_t), gb[co] = sum_p g[co](p):
+//                 32 -> 32 layers on the tensor cores (wgrad32_tc_kernel), the 1 -> 32 and
+//                 32 -> 1 layers register-blocked on CUDA cores, persistent CTAs reduced
+//                 with atomics;
 //   mse, adam, image generator.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -358,96 +360,231 @@ __global__ void __launch_bounds__(kTcThreads, 2) conv32_tc_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient of a 32 -> 32 layer, register-blocked: thread (co4, ci2, half) keeps
-// gw[co4*4 + i][ci2*2 + j][t] for i < 4, j < 2, t < 9 (72 sums) over rows half*8 .. +7
-// of every 16 x 16 tile it visits, sliding a 3 x 3 window of x along each row (three new
-// values per pixel and input channel), so each pixel costs 10 shared loads for 72 FMAs.
-// Persistent CTAs (two per SM) accumulate over many tiles and add their sums to gw with
-// one atomic per value at the end.
+// Weight gradient of a 32 -> 32 layer on the tensor cores (tcgen05):
+//     gw[co][ci][t] = sum_p g[co](p) x[ci](p + d_t),  d_t = (dy, dx),
+// a contraction over the pixels.  Per tile of 4 x 32 pixels and per dy it is one GEMM
+// D_dy[m][co] += sum_k A[m][k] B[co][k], with K the tile's 128 pixels:
+//   A rows m = ((dx + 1) 32 + ci) 2 + h hold part h (hi, lo BF16 split of FP32) of x[ci]
+//     over the tile's 6 halo rows, shifted by dx (three copies), K index 32 r + c for halo
+//     row r, tile column c; the rows of tap dy are K offset 32 (dy + 1) of that, so every
+//     tap is a descriptor offset;
+//   B rows co hold part h' of g[co] over the tile (0 outside the image), K index 32 y + c.
+// MMAs with B = g_hi and B = g_lo into the same accumulator give, summed over the two A
+// rows of (dx, ci), x_hi g_hi + x_hi g_lo + x_lo g_hi + x_lo g_lo: FP32-accurate products
+// with FP32 accumulation.  The 192 A rows form two M = 128 blocks (the second one's last
+// 64 rows are never read back); per tile 3 dy x 2 blocks x 8 K steps x 2 = 96 MMAs with
+// N = 32 into six 32-column accumulators that stay in tensor memory for all the tiles of a
+// persistent CTA; the CTA adds them to gw with atomics at the end.  The bias gradient
+// gb[co] = sum_p g[co](p) is summed by the threads that stage g.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCThreads, 2) wgrad32_kernel(const float* __restrict__ x,
-                                                               const float* __restrict__ g,
-                                                               float* __restrict__ gw, float* __restrict__ gb,
-                                                               int B, int H, int W)
+constexpr int kWgThreads = 256;
+constexpr int kWgRows = 4, kWgCols = 32;                 // tile: 128 pixels
+constexpr int kWgArows = 192;                            // (dx, ci, h)
+constexpr int kWgAplane = kWgArows * 128;                // one K atom (64 BF16) of every A row
+constexpr int kWgBplane = kWide * 128;                   // one K atom of every B row
+constexpr int kWgSmem = 3 * kWgAplane + 4 * kWgBplane + 1024;
+constexpr int kWgTmemCols = 256;                         // 6 accumulators of 32 columns
+
+__global__ void __launch_bounds__(kWgThreads, 2) wgrad32_tc_kernel(const float* __restrict__ x,
+                                                                   const float* __restrict__ g,
+                                                                   float* __restrict__ gw,
+                                                                   float* __restrict__ gb, int B,
+                                                                   int H, int W, int* status)
 {
-    extern __shared__ float csm[];
-    float* xs = csm;                          // [32][18][18]
-    float* gs = csm + kWide * kHalo * kHalo;  // [32][16 * 16 + 1]
-    const int tid = threadIdx.x;
-    const int half = tid >> 7, rem = tid & 127, ci2 = rem >> 3, co4 = rem & 7;
-    const int64_t plane = (int64_t)H * W;
-    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-    const int n_tiles = B * tiles_x * tiles_y;
-    float acc[4][2][9];
-    float accb[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        accb[i] = 0.f;
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int t = 0; t < 9; ++t) acc[i][j][t] = 0.f;
+    using namespace mci;
+    extern __shared__ __align__(1024) unsigned char wsm_raw[];
+    char* A = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(wsm_raw) + 1023) & ~uintptr_t(1023));
+    char* Bm = A + 3 * kWgAplane;   // [h'][K atom][co][128 B]; the second A block's unread rows
+                                    // of the last plane overlap its start
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort, s_drained;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(kWgTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (tid == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_bf16_f32(128, kWide);
+
+    const int64_t plane = (int64_t)H * W;
+    const int tiles_x = (W + kWgCols - 1) / kWgCols, tiles_y = (H + kWgRows - 1) / kWgRows;
+    const int n_tiles = B * tiles_y * tiles_x;
+    // B staging: thread (co = tid / 8, chunk = tid % 8) owns 16 pixels: tile row chunk / 2,
+    // columns 16 (chunk % 2) .. + 15; it also sums them for the bias gradient
+    const int bco = tid >> 3, bch = tid & 7, brow = bch >> 1, bc0 = (bch & 1) * 16;
+    // A staging: items tid + 256 i, i < 3, of (ci, halo row r, 8-column chunk q): the 10 values
+    // at columns x0 + 8q - 1 .. x0 + 8q + 8 feed the chunks of all three dx copies
+    const bool vec = (W & 3) == 0;
+    float xv[3][10], gv[16];
+    auto tile_origin = [&](int tile, int& b, int& y0, int& x0) {
+        b = tile / (tiles_y * tiles_x);
+        const int r2 = tile - b * tiles_y * tiles_x;
+        y0 = (r2 / tiles_x) * kWgRows;
+        x0 = (r2 % tiles_x) * kWgCols;
+    };
+    auto load = [&](int tile) {
+        if (tile >= n_tiles) return;
+        int b, y0, x0;
+        tile_origin(tile, b, y0, x0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int it = tid + kWgThreads * i, q = it & 3, r = (it >> 2) % 6, ci = it / 24;
+            const float* src = x + ((int64_t)b * kWide + ci) * plane + (int64_t)wrapg(y0 - 1 + r, H) * W;
+            const int c0 = x0 + 8 * q;
+            if (vec && c0 >= 1 && c0 + 8 < W) {
+                const float4 u0 = __ldg(reinterpret_cast<const float4*>(src + c0));
+                const float4 u1 = __ldg(reinterpret_cast<const float4*>(src + c0 + 4));
+                xv[i][0] = __ldg(src + c0 - 1);
+                xv[i][1] = u0.x; xv[i][2] = u0.y; xv[i][3] = u0.z; xv[i][4] = u0.w;
+                xv[i][5] = u1.x; xv[i][6] = u1.y; xv[i][7] = u1.z; xv[i][8] = u1.w;
+                xv[i][9] = __ldg(src + c0 + 8);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 10; ++e) xv[i][e] = __ldg(src + wrapg(c0 - 1 + e, W));
+            }
+        }
+        const int yy = y0 + brow, xb = x0 + bc0;
+        const float* gsrc = g + ((int64_t)b * kWide + bco) * plane + (int64_t)yy * W + xb;
+        if (vec && yy < H && xb + 15 < W) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float4 u = __ldg(reinterpret_cast<const float4*>(gsrc) + e);
+                gv[4 * e] = u.x; gv[4 * e + 1] = u.y; gv[4 * e + 2] = u.z; gv[4 * e + 3] = u.w;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) gv[e] = (yy < H && xb + e < W) ? __ldg(gsrc + e) : 0.f;
+        }
+    };
+    auto split8 = [](const float* v, uint4& hi, uint4& lo) {
+        uint32_t ph[4], pl[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]), h1 = __float2bfloat16_rn(v[2 * e + 1]);
+            ph[e] = bf16_pair_bits(h0, h1);
+            pl[e] = bf16_pair_bits(__float2bfloat16_rn(v[2 * e] - __bfloat162float(h0)),
+                                   __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1)));
+        }
+        hi = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+        lo = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    };
+    float gsum = 0.f;
+    auto stage = [&]() {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int it = tid + kWgThreads * i, q = it & 3, r = (it >> 2) % 6, ci = it / 24;
+            const int k = 32 * r + 8 * q;
+            char* pa = A + (k >> 6) * kWgAplane;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {   // copy dx, K chunk k: columns x0 + 8q + dx ..
+                uint4 hi, lo;
+                split8(&xv[i][dx + 1], hi, lo);
+                const int m = ((dx + 1) * kWide + ci) * 2;
+                *reinterpret_cast<uint4*>(pa + sw128_offset(m, k & 63)) = hi;
+                *reinterpret_cast<uint4*>(pa + sw128_offset(m + 1, k & 63)) = lo;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) gsum += gv[e];
+        const int k = 32 * brow + bc0;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+            uint4 hi, lo;
+            split8(&gv[8 * hf], hi, lo);
+            const int kk = k + 8 * hf;
+            *reinterpret_cast<uint4*>(Bm + (0 * 2 + (kk >> 6)) * kWgBplane + sw128_offset(bco, kk & 63)) = hi;
+            *reinterpret_cast<uint4*>(Bm + (1 * 2 + (kk >> 6)) * kWgBplane + sw128_offset(bco, kk & 63)) = lo;
+        }
+    };
+    uint32_t phase = 0;
+    bool first = true;
+    // software pipeline: stage tile k from registers, issue its MMAs, load tile k + 1 into
+    // registers while they run, then wait for them (they read the shared memory)
+    load(blockIdx.x);
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int b = tile / (tiles_x * tiles_y);
-        const int r2 = tile - b * tiles_x * tiles_y;
-        const int y0 = (r2 / tiles_x) * kTile, x0 = (r2 % tiles_x) * kTile;
-        __syncthreads();   // the previous tile's reads are done
-        for (int i = tid; i < kWide * kHalo * kHalo; i += kCThreads) {
-            const int ci = i / (kHalo * kHalo), r = i % (kHalo * kHalo);
-            const int yy = wrap(y0 + r / kHalo - 1, H), xx = wrap(x0 + r % kHalo - 1, W);
-            xs[i] = x[((int64_t)b * kWide + ci) * plane + (int64_t)yy * W + xx];
-        }
-        for (int i = tid; i < kWide * kTile * kTile; i += kCThreads) {
-            const int co = i / (kTile * kTile), r = i % (kTile * kTile);
-            const int yy = y0 + r / kTile, xx = x0 + r % kTile;
-            gs[co * kGStride + r] =
-                (yy < H && xx < W) ? g[((int64_t)b * kWide + co) * plane + (int64_t)yy * W + xx] : 0.f;
-        }
+        stage();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int dyi = 0; dyi < 3; ++dyi)
+#pragma unroll
+                for (int mb = 0; mb < 2; ++mb) {
+                    const uint32_t d = tmem + (uint32_t)((dyi * 2 + mb) * 32);
+#pragma unroll
+                    for (int hp = 0; hp < 2; ++hp)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int ka = 32 * dyi + 16 * j, kb = 16 * j;
+                            const uint32_t a = smem_u32(A + (ka >> 6) * kWgAplane + mb * 128 * 128) + (ka & 63) * 2;
+                            const uint32_t bb = smem_u32(Bm + (hp * 2 + (kb >> 6)) * kWgBplane) + (kb & 63) * 2;
+                            mma_bf16(d, smem_desc_sw128(a), smem_desc_sw128(bb), idesc, !(first && hp == 0 && j == 0));
+                        }
+                }
+            mma_commit(smem_u32(&bar));
+        }
+        load(tile + gridDim.x);
+        first = false;
+        if (!mbar_wait(smem_u32(&bar), phase)) {
+            atomicOr(status, 1);
+            s_abort = 1;
+        }
+        phase ^= 1;
+        __syncthreads();
+        if (s_abort) break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!s_abort && !first) {
+        // warp w reads TMEM lanes (A rows) 32 (w % 4) .. + 31, columns (co) 16 (w / 4) .. + 15
+        const int quarter = warp & 3, half = warp >> 2;
 #pragma unroll 1
-        for (int r = half * 8; r < half * 8 + 8; ++r) {
-            float win[2][3][3];
+        for (int acc = 0; acc < 6; ++acc) {
+            const int dyi = acc >> 1, mb = acc & 1;
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 32 + half * 16), v);
+            const int m = mb * 128 + quarter * 32 + lane;   // rows m (hi) and m + 1 (lo) of (dx, ci)
+            float sv[16];
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < 16; ++j) {
+                const float f = __uint_as_float(v[j]);
+                sv[j] = f + __shfl_down_sync(0xffffffffu, f, 1);
+            }
+            if ((lane & 1) == 0 && m < kWgArows) {
+                const int dx1 = (m >> 1) / kWide, ci = (m >> 1) % kWide, t = dyi * 3 + dx1;
 #pragma unroll
-                for (int dy = 0; dy < 3; ++dy) {
-                    const float* row = xs + (ci2 * 2 + j) * kHalo * kHalo + (r + dy) * kHalo;
-                    win[j][dy][1] = row[0];
-                    win[j][dy][2] = row[1];
-                }
-#pragma unroll 4
-            for (int px = 0; px < kTile; ++px) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy) {
-                        win[j][dy][0] = win[j][dy][1];
-                        win[j][dy][1] = win[j][dy][2];
-                        win[j][dy][2] = xs[(ci2 * 2 + j) * kHalo * kHalo + (r + dy) * kHalo + px + 2];
-                    }
-                float gv[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) gv[i] = gs[(co4 * 4 + i) * kGStride + r * kTile + px];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    accb[i] += gv[i];
-#pragma unroll
-                    for (int j = 0; j < 2; ++j)
-#pragma unroll
-                        for (int t = 0; t < 9; ++t) acc[i][j][t] += gv[i] * win[j][t / 3][t % 3];
-                }
+                for (int j = 0; j < 16; ++j)
+                    atomicAdd(&gw[((int64_t)(half * 16 + j) * kWide + ci) * 9 + t], sv[j]);
             }
         }
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int co = co4 * 4 + i;
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int t = 0; t < 9; ++t) atomicAdd(&gw[((int64_t)co * kWide + ci2 * 2 + j) * 9 + t], acc[i][j][t]);
-        if (ci2 == 0) atomicAdd(&gb[co], accb[i]);
+    // bias: the 8 threads of one co are consecutive lanes
+    gsum += __shfl_xor_sync(0xffffffffu, gsum, 1);
+    gsum += __shfl_xor_sync(0xffffffffu, gsum, 2);
+    gsum += __shfl_xor_sync(0xffffffffu, gsum, 4);
+    if (!s_abort && bch == 0) atomicAdd(&gb[bco], gsum);
+    // after a timeout the committed MMAs may still write the accumulators: wait for their
+    // commit once more (bounded) and free the tensor memory only once they are done; if they
+    // never finish it stays allocated (the status word already reports the timeout)
+    if (s_abort) {
+        if (tid == 0) s_drained = mbar_wait(smem_u32(&bar), phase ^ 1) ? 1 : 0;
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0 && (!s_abort || s_drained)) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgTmemCols)
+                     : "memory");
     }
 }
 
@@ -679,6 +816,7 @@ int tc_grid_limit()
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         n = 2 * (sms > 0 ? sms : 1);
         cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+        cudaFuncSetAttribute(wgrad32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
     }
     return n;
 }
@@ -706,7 +844,7 @@ cudaError_t conv(const float* x, int cin, int cout, const __nv_bfloat16* w, bool
 }
 
 cudaError_t wgrad(int l, const float* x, const float* g, float* gw, float* gb, int B, int H, int W,
-                  cudaStream_t s)
+                  cudaStream_t s, int* status)
 {
     const int tiles = B * ((H + kTile - 1) / kTile) * ((W + kTile - 1) / kTile);
     const int grid = tiles < tc_grid_limit() ? tiles : tc_grid_limit();
@@ -717,8 +855,10 @@ cudaError_t wgrad(int l, const float* x, const float* g, float* gw, float* gb, i
     } else if (cout == 1) {
         wgrad_narrow_kernel<kWide, 1><<<grid, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
     } else {
-        cudaFuncSetAttribute(wgrad32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        wgrad32_kernel<<<grid, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
+        // 32 -> 32: tensor cores, tiles of 4 x 32 pixels
+        const int tc_tiles = B * ((H + kWgRows - 1) / kWgRows) * ((W + kWgCols - 1) / kWgCols);
+        const int tc_grid = tc_tiles < tc_grid_limit() ? tc_tiles : tc_grid_limit();
+        wgrad32_tc_kernel<<<tc_grid, kWgThreads, kWgSmem, s>>>(x, g, gw, gb, B, H, W, status);
     }
     return cudaGetLastError();
 }
@@ -753,7 +893,7 @@ cudaError_t backward(mci_corrector_t c, const float* mci, const float* gpred, in
     int gi = 0;
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         const float* x = l == 0 ? mci : hidden(c, l - 1, pix);
-        e = wgrad(l, x, g, c->grad + c->woff[l], c->grad + c->boff[l], B, H, W, s);
+        e = wgrad(l, x, g, c->grad + c->woff[l], c->grad + c->boff[l], B, H, W, s, c->status);
         if (l > 0 && e == cudaSuccess) {
             // gradient with respect to layer l's input: conv with transposed, reversed weights
             float* gin = c->gbuf[gi];
