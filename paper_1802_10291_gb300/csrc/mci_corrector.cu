@@ -36,7 +36,6 @@ namespace {
 constexpr int kTile = 16;          // output tile edge
 constexpr int kHalo = kTile + 2;   // input tile edge
 constexpr int kCThreads = kTile * kTile;
-constexpr int kGStride = kTile * kTile + 1;   // per-channel stride of the gradient tile (wgrad)
 constexpr int kWide = 32;          // hidden channels
 constexpr int kLayers = 5;
 __host__ __device__ constexpr int cin_of(int l) { return l == 0 ? 1 : kWide; }
@@ -588,74 +587,183 @@ __global__ void __launch_bounds__(kWgThreads, 2) wgrad32_tc_kernel(const float* 
     }
 }
 
-// Weight gradient of the 1 -> 32 and 32 -> 1 layers: thread (c, rows) with c = tid % 32 the
-// wide channel keeps the 9 tap sums of pair (c, 0) over rows 2 (tid / 32) .. + 1 of every
-// tile, sliding a 3 x 3 window of x along each row; persistent CTAs, one atomic per sum.
+// ---------------------------------------------------------------------------
+// Narrow layers (1 -> 32 and 32 -> 1) on CUDA cores, tiles of 8 rows x 32 columns: lane =
+// image column (every row access of a warp is one coalesced segment), warp w takes the wide
+// channels w, w + 8, w + 16, w + 24, and a 3 x 3 window slides down the tile's rows (one new
+// row of three columns per step, read through L1).  Persistent CTAs; weight gradients are
+// reduced over the warp's lanes and added with one atomic per (channel, tap) and warp.
+// ---------------------------------------------------------------------------
+constexpr int kNRows = 8, kNCols = 32, kNThreads = 256;
+
+// Row yy (already wrapped) of one channel plane at the lane's three columns cm, c0, cp.
+__device__ __forceinline__ void load3(const float* __restrict__ p, int yy, int W, int cm, int c0, int cp,
+                                      float (&v)[3])
+{
+    const float* row = p + (int64_t)yy * W;
+    v[0] = __ldg(row + cm);
+    v[1] = __ldg(row + c0);
+    v[2] = __ldg(row + cp);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// 32 -> 1 convolution (the last layer): out = bias + sum_ci sum_t w[ci][t] x[ci](p + d_t), then
+// optional ReLU, residual add and mask as in conv3x3_kernel.  One tile per CTA; each warp sums
+// its four channels, the eight partial sums of a pixel are added through shared memory.
+__global__ void __launch_bounds__(kNThreads) conv32to1_kernel(const float* __restrict__ x,
+                                                              const __nv_bfloat16* __restrict__ w,
+                                                              bool transposed_w, const float* __restrict__ bias,
+                                                              const float* __restrict__ out_mask,
+                                                              const float* __restrict__ res,
+                                                              float* __restrict__ out, int H, int W, bool relu)
+{
+    __shared__ float red[kNThreads / 32][kNRows][kNCols];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.z, y0 = blockIdx.y * kNRows, col = blockIdx.x * kNCols + lane;
+    const int64_t plane = (int64_t)H * W;
+    const int cm = wrapg(col - 1, W), c0 = wrapg(col, W), cp = wrapg(col + 1, W);
+    float part[kNRows];
+#pragma unroll
+    for (int r = 0; r < kNRows; ++r) part[r] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int ci = warp + 8 * j;
+        float wv[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+            wv[t] = __bfloat162float(transposed_w ? w[(int64_t)ci * 9 + (8 - t)] : w[(int64_t)ci * 9 + t]);
+        const float* xp = x + ((int64_t)b * kWide + ci) * plane;
+        float w0[3], w1[3], w2[3];
+        load3(xp, wrapg(y0 - 1, H), W, cm, c0, cp, w0);
+        load3(xp, wrapg(y0, H), W, cm, c0, cp, w1);
+#pragma unroll
+        for (int r = 0; r < kNRows; ++r) {
+            load3(xp, wrapg(y0 + r + 1, H), W, cm, c0, cp, w2);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) part[r] += wv[d] * w0[d] + wv[3 + d] * w1[d] + wv[6 + d] * w2[d];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                w0[d] = w1[d];
+                w1[d] = w2[d];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kNRows; ++r) red[warp][r][lane] = part[r];
+    __syncthreads();
+    const int r = warp, y = y0 + r;   // thread (r, lane) finishes pixel (y0 + r, col)
+    if (y < H && col < W) {
+        float v = bias ? bias[0] : 0.f;
+#pragma unroll
+        for (int k = 0; k < kNThreads / 32; ++k) v += red[k][r][lane];
+        const int64_t o = (int64_t)b * plane + (int64_t)y * W + col;
+        if (relu) v = fmaxf(v, 0.f);
+        if (res) v += res[o];
+        if (out_mask && !(out_mask[o] > 0.f)) v = 0.f;
+        out[o] = v;
+    }
+}
+
+// gw[co][ci][t] = sum_p g[co](p) x[ci](p + d_t), gb[co] = sum_p g[co](p) for the layers with one
+// narrow side: CIN = 32, COUT = 1 (the last layer: the wide side is x) or CIN = 1, COUT = 32
+// (the first layer: the wide side is g).
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kCThreads, 2) wgrad_narrow_kernel(const float* __restrict__ x,
+__global__ void __launch_bounds__(kNThreads, 2) wgrad_narrow_kernel(const float* __restrict__ x,
                                                                     const float* __restrict__ g,
                                                                     float* __restrict__ gw,
                                                                     float* __restrict__ gb, int B, int H,
                                                                     int W)
 {
     static_assert((CIN == 1 && COUT == kWide) || (CIN == kWide && COUT == 1), "one narrow side");
-    extern __shared__ float csm[];
-    float* xs = csm;                          // [CIN][18][18]
-    float* gs = csm + CIN * kHalo * kHalo;    // [COUT][16 * 16 + 1]
-    const int tid = threadIdx.x;
-    const int c = tid & 31, rg = tid >> 5;    // wide channel, row pair
-    const int ci = CIN == 1 ? 0 : c, co = COUT == 1 ? 0 : c;
+    constexpr bool WIDE_X = CIN == kWide;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t plane = (int64_t)H * W;
-    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+    const int tiles_x = (W + kNCols - 1) / kNCols, tiles_y = (H + kNRows - 1) / kNRows;
     const int n_tiles = B * tiles_x * tiles_y;
-    float acc[9], accb = 0.f;
+    float acc[4][9], accb[4];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+    for (int j = 0; j < 4; ++j) {
+        accb[j] = 0.f;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc[j][t] = 0.f;
+    }
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int b = tile / (tiles_x * tiles_y);
         const int r2 = tile - b * tiles_x * tiles_y;
-        const int y0 = (r2 / tiles_x) * kTile, x0 = (r2 % tiles_x) * kTile;
-        __syncthreads();
-        for (int i = tid; i < CIN * kHalo * kHalo; i += kCThreads) {
-            const int cc = i / (kHalo * kHalo), r = i % (kHalo * kHalo);
-            const int yy = wrap(y0 + r / kHalo - 1, H), xx = wrap(x0 + r % kHalo - 1, W);
-            xs[i] = x[((int64_t)b * CIN + cc) * plane + (int64_t)yy * W + xx];
-        }
-        for (int i = tid; i < COUT * kTile * kTile; i += kCThreads) {
-            const int cc = i / (kTile * kTile), r = i % (kTile * kTile);
-            const int yy = y0 + r / kTile, xx = x0 + r % kTile;
-            gs[cc * kGStride + r] =
-                (yy < H && xx < W) ? g[((int64_t)b * COUT + cc) * plane + (int64_t)yy * W + xx] : 0.f;
-        }
-        __syncthreads();
-        const float* xc = xs + ci * kHalo * kHalo;
-        const float* gc = gs + co * kGStride;
-#pragma unroll 1
-        for (int r = rg * 2; r < rg * 2 + 2; ++r) {
-            float win[3][3];
+        const int y0 = (r2 / tiles_x) * kNRows, col = (r2 % tiles_x) * kNCols + lane;
+        const bool in_w = col < W;
+        const int cm = wrapg(col - 1, W), c0 = wrapg(col, W), cp = wrapg(col + 1, W);
+        if constexpr (WIDE_X) {
+            // the one gradient channel at the tile's pixels, then the 32 x channels
+            float gv[kNRows];
 #pragma unroll
-            for (int dy = 0; dy < 3; ++dy) {
-                win[dy][1] = xc[(r + dy) * kHalo];
-                win[dy][2] = xc[(r + dy) * kHalo + 1];
-            }
-#pragma unroll 4
-            for (int px = 0; px < kTile; ++px) {
+            for (int r = 0; r < kNRows; ++r)
+                gv[r] = (in_w && y0 + r < H) ? __ldg(g + (int64_t)b * plane + (int64_t)(y0 + r) * W + col) : 0.f;
 #pragma unroll
-                for (int dy = 0; dy < 3; ++dy) {
-                    win[dy][0] = win[dy][1];
-                    win[dy][1] = win[dy][2];
-                    win[dy][2] = xc[(r + dy) * kHalo + px + 2];
+            for (int r = 0; r < kNRows; ++r) accb[0] += gv[r];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float* xp = x + ((int64_t)b * kWide + warp + 8 * j) * plane;
+                float w0[3], w1[3], w2[3];
+                load3(xp, wrapg(y0 - 1, H), W, cm, c0, cp, w0);
+                load3(xp, wrapg(y0, H), W, cm, c0, cp, w1);
+#pragma unroll
+                for (int r = 0; r < kNRows; ++r) {
+                    load3(xp, wrapg(y0 + r + 1, H), W, cm, c0, cp, w2);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        acc[j][d] += gv[r] * w0[d];
+                        acc[j][3 + d] += gv[r] * w1[d];
+                        acc[j][6 + d] += gv[r] * w2[d];
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        w0[d] = w1[d];
+                        w1[d] = w2[d];
+                    }
                 }
-                const float gv = gc[r * kTile + px];
-                accb += gv;
+            }
+        } else {
+            // the one x channel around the tile, then the 32 gradient channels
+            float xw[kNRows + 2][3];
 #pragma unroll
-                for (int t = 0; t < 9; ++t) acc[t] += gv * win[t / 3][t % 3];
+            for (int r = 0; r < kNRows + 2; ++r) load3(x + (int64_t)b * plane, wrapg(y0 - 1 + r, H), W, cm, c0, cp, xw[r]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float* gp = g + ((int64_t)b * kWide + warp + 8 * j) * plane;
+#pragma unroll
+                for (int r = 0; r < kNRows; ++r) {
+                    const float gv = (in_w && y0 + r < H) ? __ldg(gp + (int64_t)(y0 + r) * W + col) : 0.f;
+                    accb[j] += gv;
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) acc[j][t] += gv * xw[r + t / 3][t % 3];
+                }
             }
         }
     }
 #pragma unroll
-    for (int t = 0; t < 9; ++t) atomicAdd(&gw[((int64_t)co * CIN + ci) * 9 + t], acc[t]);
-    if (COUT == kWide || c == 0) atomicAdd(&gb[co], accb);
+    for (int j = 0; j < 4; ++j) {
+        const int c = warp + 8 * j;   // the wide channel
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const float v = warp_sum(acc[j][t]);
+            if (lane == 0) atomicAdd(&gw[(int64_t)c * 9 + t], v);   // [co][ci][t] with one side 1
+        }
+        if (!WIDE_X) {
+            const float v = warp_sum(accb[j]);
+            if (lane == 0) atomicAdd(&gb[c], v);
+        }
+    }
+    if (WIDE_X && warp == 0) {
+        const float v = warp_sum(accb[0]);
+        if (lane == 0) atomicAdd(&gb[0], v);
+    }
 }
 
 // d pred: grad = 2 (pred - hr) / n, loss += sum (pred - hr)^2 / n
@@ -837,6 +945,9 @@ cudaError_t conv(const float* x, int cin, int cout, const __nv_bfloat16* w, bool
     if (cout == kWide) {
         cudaFuncSetAttribute(conv3x3_kernel<kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         conv3x3_kernel<kWide><<<grid, kCThreads, smem, s>>>(x, cin, w, tw, bias, out_mask, res, out, H, W, relu);
+    } else if (cin == kWide) {
+        const dim3 ngrid((W + kNCols - 1) / kNCols, (H + kNRows - 1) / kNRows, B);
+        conv32to1_kernel<<<ngrid, kNThreads, 0, s>>>(x, w, tw, bias, out_mask, res, out, H, W, relu);
     } else {
         conv3x3_kernel<1><<<grid, kCThreads, smem, s>>>(x, cin, w, tw, bias, out_mask, res, out, H, W, relu);
     }
@@ -846,14 +957,13 @@ cudaError_t conv(const float* x, int cin, int cout, const __nv_bfloat16* w, bool
 cudaError_t wgrad(int l, const float* x, const float* g, float* gw, float* gb, int B, int H, int W,
                   cudaStream_t s, int* status)
 {
-    const int tiles = B * ((H + kTile - 1) / kTile) * ((W + kTile - 1) / kTile);
+    const int tiles = B * ((H + kNRows - 1) / kNRows) * ((W + kNCols - 1) / kNCols);
     const int grid = tiles < tc_grid_limit() ? tiles : tc_grid_limit();
     const int cin = cin_of(l), cout = cout_of(l);
-    const size_t smem = sizeof(float) * (cin * kHalo * kHalo + cout * kGStride);
     if (cin == 1) {
-        wgrad_narrow_kernel<1, kWide><<<grid, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
+        wgrad_narrow_kernel<1, kWide><<<grid, kNThreads, 0, s>>>(x, g, gw, gb, B, H, W);
     } else if (cout == 1) {
-        wgrad_narrow_kernel<kWide, 1><<<grid, kCThreads, smem, s>>>(x, g, gw, gb, B, H, W);
+        wgrad_narrow_kernel<kWide, 1><<<grid, kNThreads, 0, s>>>(x, g, gw, gb, B, H, W);
     } else {
         // 32 -> 32: tensor cores, tiles of 4 x 32 pixels
         const int tc_tiles = B * ((H + kWgRows - 1) / kWgRows) * ((W + kWgCols - 1) / kWgCols);
