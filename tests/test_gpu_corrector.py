@@ -38,7 +38,10 @@ def _oracle_params(p32):
     return p
 
 
-@pytest.mark.parametrize("shape", [(2, 20, 24), (1, 33, 17), (3, 16, 16), (1, 37, 70)])
+# (1, 12, 96) and (2, 9, 100): rows of 16-byte-aligned tiles inside the image (vector loads)
+# next to tiles at the right edge (wrapped columns)
+@pytest.mark.parametrize("shape", [(2, 20, 24), (1, 33, 17), (3, 16, 16), (1, 37, 70), (1, 12, 96),
+                                   (2, 9, 100)])
 def test_forward_and_gradient_parity(cuda_device, shape):
     import torch
     from paper_1802_10291_gb300 import corrector
