@@ -241,8 +241,9 @@ def oracle_sample(batch, n_per_class=2, seed=0):
     return sorted(idx)
 
 
-def run_oracle(batch, idx):
-    """FP64 oracle (direct sum formula) on the signals idx; returns {b: [1, T]} and seconds."""
+def run_oracle(batch, idx, nthreads=0):
+    """FP64 oracle (direct sum formula) on the signals idx; returns {b: [1, T]} and seconds.
+    nthreads = 0: all host cores."""
     import oracle
     t0 = time.perf_counter()
     res = {}
@@ -251,7 +252,7 @@ def run_oracle(batch, idx):
         if not sel:
             continue
         g = np.stack([batch["g"][b] for b in sel])
-        out = oracle.mci_direct(SYSTEMS, g, S_FACTOR * P)
+        out = oracle.mci_direct(SYSTEMS, g, S_FACTOR * P, nthreads=nthreads)
         for i, b in enumerate(sel):
             res[b] = out[i]
     return res, time.perf_counter() - t0
@@ -856,6 +857,12 @@ def main():
                "kind": "oracle",
                "sample": f"{len(idx)} signals, {CPU_PER_CLASS} of each P class (half trig, half smooth), "
                          f"FP64 direct sum formula, {cpu_s:.1f} s"}
+        # the same oracle on one core, on 2 signals of each class (a few seconds)
+        idx1 = oracle_sample(batch, n_per_class=2, seed=1)
+        _, cpu1_s = run_oracle(batch, idx1, nthreads=1)
+        n1 = sum(S_FACTOR * int(batch["P"][b]) for b in idx1)
+        cpu["one_core"] = {"value": n1 / cpu1_s / 1e6, "unit": UNIT, "cores": 1,
+                           "sample": f"{len(idx1)} signals, 2 of each P class, {cpu1_s:.1f} s"}
 
     if rank == 0:
         line = {

@@ -331,6 +331,29 @@ mci_status mci_destroy(mci_plan_t plan);
 /* mci_error_string -- static description of a status code. */
 const char* mci_error_string(mci_status status);
 
+/*
+ * mci_debug_fail_allocation -- test hook: the device and page-locked allocations made by
+ * mci_plan and mci_interp_1d_host succeed `after` more times, then one is refused as if the
+ * device were out of memory (the call returns MCI_ERR_OOM and frees what it had allocated);
+ * after that, allocations succeed again.  A negative value switches the hook off (the default).
+ * Process-wide; not for use while other threads create plans.  The paper has no counterpart:
+ * it lets the out-of-memory paths be tested without exhausting a GPU.
+ */
+void mci_debug_fail_allocation(int after);
+
+/*
+ * mci_tune_cache_save / mci_tune_cache_load -- the tile heights picked by the plan-time
+ * autotuner (mci_desc.autotune) are kept process-wide, keyed by kernel kind, precision, real
+ * or complex signals, P, T, input channels, output phases and device (name and
+ * multiprocessor count); a plan whose class has an entry uses it without timing.  save writes
+ * them to `path` as a flat JSON object {"key": tile_height, ...}; load merges such a file
+ * (keys as save writes them, values 1 .. 64).  Host only: no device work.  Errors:
+ * MCI_ERR_INVALID_ARG for a NULL path, a file that cannot be opened or a malformed file
+ * (nothing is merged then).  The paper has no counterpart: an interface of this library.
+ */
+mci_status mci_tune_cache_save(const char* path);
+mci_status mci_tune_cache_load(const char* path);
+
 #ifdef __cplusplus
 }
 #endif

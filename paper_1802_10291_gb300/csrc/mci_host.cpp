@@ -3,11 +3,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "mci_internal.h"
@@ -317,6 +322,29 @@ struct mci_plan_s {
 };
 
 namespace {
+
+// Test hook of mci_debug_fail_allocation: allocations left before one is refused (-1: off).
+std::atomic<int> g_fail_after{-1};
+
+bool refuse_allocation()
+{
+    int c = g_fail_after.load();
+    while (c >= 0 && !g_fail_after.compare_exchange_weak(c, c - 1)) {
+    }
+    return c == 0;
+}
+
+cudaError_t dev_malloc(void** ptr, size_t bytes)
+{
+    if (refuse_allocation()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(ptr, bytes);
+}
+
+cudaError_t pinned_alloc(void** ptr, size_t bytes)
+{
+    if (refuse_allocation()) return cudaErrorMemoryAllocation;
+    return cudaHostAlloc(ptr, bytes, cudaHostAllocDefault);
+}
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -865,22 +893,53 @@ mci_status mci_destroy(mci_plan_t p)
 // scratch batch for each candidate tile height G (signals per CTA; the candidates come
 // from shared-memory budgets of 16 .. 144 KB per CTA, i.e. 1 .. 12 CTAs per SM) and keep
 // the fastest.  The results of a launch do not depend on G.
+// Tile heights chosen by the autotuner, process-wide, keyed by the kernel kind, the class
+// shape, the precision and the device (name and multiprocessor count); saved to and loaded
+// from a JSON object {"key": G, ...} by mci_tune_cache_save / mci_tune_cache_load.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+
+static std::string tune_key(const ClassDev& c, int prec, const cudaDeviceProp& prop)
+{
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "generic-1d|%s|%s|P=%d|T=%d|Min=%d|Q=%d|%s|sm=%d",
+                  prec == MCI_FP64 ? "fp64" : "fp32", c.cplx ? "complex" : "real", c.P, c.T, c.M_in, c.Q,
+                  prop.name, prop.multiProcessorCount);
+    return buf;
+}
+
 static cudaError_t autotune_tiles(mci_plan_s* p, int smem_cap, cudaStream_t s)
 {
     const int n = (int)p->cls.size();
     const int csz = (int)(2 * p->elem);
     const size_t scratch_bytes = (size_t)64 << 20;
     void* scratch = nullptr;
-    cudaError_t e = cudaMalloc(&scratch, scratch_bytes);
+    cudaError_t e = dev_malloc((void**)&scratch, scratch_bytes);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(scratch, 0, scratch_bytes, s);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    cudaDeviceProp prop{};
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
     for (int c = 0; c < n && e == cudaSuccess; ++c) {
         ClassDev cd = p->cdev[c];
         if (cd.fast) continue;   // the fused kernel's tile is fixed by N
         const int per = cd.sstride * csz;
+        const std::string key = tune_key(cd, p->desc.precision, prop);
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tune.find(key);
+            const int twb0 = smem_twiddle_count(cd.N) * csz;
+            if (it != g_tune.end() && it->second >= 1 && it->second <= kMaxTile &&
+                it->second * per + twb0 <= smem_cap) {   // tuned before: no timing
+                p->cdev[c].G = it->second;
+                p->csmem[c] = it->second * per + twb0;
+                continue;
+            }
+        }
         const int twb = smem_twiddle_count(cd.N) * csz;
         const int64_t sig_bytes = (cd.in_len + cd.out_len) * (int64_t)p->elem;
         const int64_t nsig = std::max<int64_t>(1, std::min<int64_t>((int64_t)scratch_bytes / sig_bytes, 8192));
@@ -923,6 +982,8 @@ static cudaError_t autotune_tiles(mci_plan_s* p, int smem_cap, cudaStream_t s)
         }
         p->cdev[c].G = bestG;
         p->csmem[c] = bestG * per + twb;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = bestG;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -1057,7 +1118,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     const size_t order_bytes = align_up(sizeof(int) * n, 256);
     const size_t total = launch_bytes + order_bytes + align_up(W_bytes, 256);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMalloc(&p->d_tables, total);
+    cudaError_t e = dev_malloc((void**)&p->d_tables, total);
     if (e != cudaSuccess) {
         delete p;
         return cuda_status(e);
@@ -1130,7 +1191,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_W, W_src, W_bytes, cudaMemcpyHostToDevice, s);
     p->d_kmap.assign(n, nullptr);
     if (e == cudaSuccess && !p->gemm_tab.empty()) {
-        e = cudaMalloc(&p->d_gemm, sizeof(float) * p->gemm_tab.size());
+        e = dev_malloc((void**)&p->d_gemm, sizeof(float) * p->gemm_tab.size());
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->d_gemm, p->gemm_tab.data(), sizeof(float) * p->gemm_tab.size(),
                                 cudaMemcpyHostToDevice, s);
@@ -1141,7 +1202,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     }
 
     if (e == cudaSuccess && !p->rtab.empty()) {
-        e = cudaMalloc(&p->d_rtab, sizeof(double) * p->rtab.size());
+        e = dev_malloc((void**)&p->d_rtab, sizeof(double) * p->rtab.size());
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->d_rtab, p->rtab.data(), sizeof(double) * p->rtab.size(), cudaMemcpyHostToDevice,
                                 s);
@@ -1177,7 +1238,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         o_jobs = carve(sizeof(GemmJob) * 2 * I);
         o_tile0 = carve(sizeof(int) * 2 * (I + 1));
     }
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_work, off);
+    if (e == cudaSuccess) e = dev_malloc((void**)&p->d_work, off);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
         mci_destroy(p);
@@ -1217,7 +1278,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         }
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-            e = cudaHostAlloc((void**)&p->h_stage[i], p->stage_bytes, cudaHostAllocDefault);
+            e = pinned_alloc((void**)&p->h_stage[i], p->stage_bytes);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_stage[i], cudaEventDisableTiming);
         }
     }
@@ -1240,7 +1301,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
         }
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-            e = cudaHostAlloc((void**)&p->h_stage2[i], p->stage2_bytes, cudaHostAllocDefault);
+            e = pinned_alloc((void**)&p->h_stage2[i], p->stage2_bytes);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_stage2[i], cudaEventDisableTiming);
         }
     }
@@ -1480,7 +1541,7 @@ mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int
         e = cudaDeviceSynchronize();
         if (e == cudaSuccess && p->d_chunk) e = cudaFree(p->d_chunk);
         p->d_chunk = nullptr;
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_chunk, mci_plan_s::kSlots * (need_in + need_out));
+        if (e == cudaSuccess) e = dev_malloc((void**)&p->d_chunk, mci_plan_s::kSlots * (need_in + need_out));
         if (e != cudaSuccess) {
             p->chunk_in_bytes = p->chunk_out_bytes = 0;
             return cuda_status(e);
@@ -1581,3 +1642,58 @@ mci_status mci_interp_1d_noalloc(mci_plan_t p, const void* in, const int64_t* in
 }
 
 }  // extern "C"
+
+void mci_debug_fail_allocation(int after) { g_fail_after.store(after < 0 ? -1 : after); }
+
+mci_status mci_tune_cache_save(const char* path)
+{
+    if (!path) return MCI_ERR_INVALID_ARG;
+    FILE* f = std::fopen(path, "w");
+    if (!f) return MCI_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::fprintf(f, "{");
+    bool first = true;
+    for (const auto& kv : g_tune) {
+        std::fprintf(f, "%s\n  \"%s\": %d", first ? "" : ",", kv.first.c_str(), kv.second);
+        first = false;
+    }
+    std::fprintf(f, "%s}\n", first ? "" : "\n");
+    return std::fclose(f) == 0 ? MCI_OK : MCI_ERR_INVALID_ARG;
+}
+
+mci_status mci_tune_cache_load(const char* path)
+{
+    if (!path) return MCI_ERR_INVALID_ARG;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return MCI_ERR_INVALID_ARG;
+    std::string txt;
+    char buf[4096];
+    size_t k;
+    while ((k = std::fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, k);
+    std::fclose(f);
+    // a flat JSON object of string keys (no escapes) and integer values
+    std::map<std::string, int> got;
+    size_t i = txt.find('{');
+    if (i == std::string::npos) return MCI_ERR_INVALID_ARG;
+    ++i;
+    for (;;) {
+        while (i < txt.size() && (txt[i] == ' ' || txt[i] == '\n' || txt[i] == '\r' || txt[i] == '\t' || txt[i] == ','))
+            ++i;
+        if (i >= txt.size()) return MCI_ERR_INVALID_ARG;
+        if (txt[i] == '}') break;
+        if (txt[i] != '"') return MCI_ERR_INVALID_ARG;
+        const size_t j = txt.find('"', i + 1);
+        if (j == std::string::npos) return MCI_ERR_INVALID_ARG;
+        const std::string key = txt.substr(i + 1, j - i - 1);
+        i = txt.find(':', j);
+        if (i == std::string::npos) return MCI_ERR_INVALID_ARG;
+        char* end = nullptr;
+        const long v = std::strtol(txt.c_str() + i + 1, &end, 10);
+        if (end == txt.c_str() + i + 1 || v < 1 || v > kMaxTile) return MCI_ERR_INVALID_ARG;
+        got[key] = (int)v;
+        i = (size_t)(end - txt.c_str());
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& kv : got) g_tune[kv.first] = kv.second;
+    return MCI_OK;
+}

@@ -109,6 +109,12 @@ def load(path: str = LIB_PATH):
         lib.mci_plan_info.restype = ctypes.c_int
         lib.mci_destroy.argtypes = [vp]
         lib.mci_destroy.restype = ctypes.c_int
+        lib.mci_tune_cache_save.argtypes = [ctypes.c_char_p]
+        lib.mci_tune_cache_save.restype = ctypes.c_int
+        lib.mci_tune_cache_load.argtypes = [ctypes.c_char_p]
+        lib.mci_tune_cache_load.restype = ctypes.c_int
+        lib.mci_debug_fail_allocation.argtypes = [ctypes.c_int]
+        lib.mci_debug_fail_allocation.restype = None
         lib.mci_error_string.argtypes = [ctypes.c_int]
         lib.mci_error_string.restype = ctypes.c_char_p
         _lib = lib
@@ -125,7 +131,7 @@ def header_functions(paths=None):
     names = set()
     for path in paths:
         text = open(path).read()
-        names |= set(re.findall(r"^\s*(?:mci_status|const char\*|int)\s+(mci\w*)\s*\(", text, re.M))
+        names |= set(re.findall(r"^\s*(?:mci_status|const char\*|int|void)\s+(mci\w*)\s*\(", text, re.M))
     return sorted(names)
 
 
@@ -250,6 +256,22 @@ def mci_interp_1d_noalloc(plan: int, inp, in_off, out, out_off, size_class, batc
 
 
 MCI_NOALLOC_MAX_BATCH = 65536
+
+
+def mci_tune_cache_save(path: str):
+    """Write the autotuner's tile heights (process-wide) to a JSON file."""
+    _check(load().mci_tune_cache_save(os.fsencode(path)), "mci_tune_cache_save")
+
+
+def mci_tune_cache_load(path: str):
+    """Merge a JSON file written by mci_tune_cache_save into the autotuner's entries."""
+    _check(load().mci_tune_cache_load(os.fsencode(path)), "mci_tune_cache_load")
+
+
+def mci_debug_fail_allocation(after: int):
+    """Test hook: the library's allocations succeed `after` more times, then one is refused
+    (MCI_ERR_OOM); negative: off."""
+    load().mci_debug_fail_allocation(int(after))
 
 
 def mci_upsample_2d(plan: int, lr, lr_off, h, w, scale, hr, hr_off, n_img: int, stream=None):

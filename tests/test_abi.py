@@ -17,7 +17,8 @@ def test_exports_every_declared_symbol(mci_lib):
                              "mci_corrector_loss_grad", "mci_corrector_train_step",
                              "mci_corrector_get_state", "mci_corrector_set_state", "mci_corrector_status",
                              "mci_corrector_destroy", "mci_generate_images", "mci_decimate", "mci_degrade",
-                             "mci2_plan", "mci2_interp", "mci2_plan_info", "mci2_destroy"}
+                             "mci2_plan", "mci2_interp", "mci2_plan_info", "mci2_destroy",
+                             "mci_debug_fail_allocation", "mci_tune_cache_save", "mci_tune_cache_load"}
     for name in declared:
         assert hasattr(mci_lib, name), name
 
@@ -146,3 +147,28 @@ def test_2d_null_arguments(mci_lib):
     assert lib.mci2_interp(None, None, None, 1, None) == mci.MCI_ERR_INVALID_ARG
     assert lib.mci2_plan_info(None, None, None, None) == mci.MCI_ERR_INVALID_ARG
     assert lib.mci2_destroy(None) == mci.MCI_OK
+
+
+def test_tune_cache_json_round_trip(tmp_path):
+    """The autotuner cache file: load merges a written object, save writes it back; malformed
+    files and values outside 1 .. 64 are refused (host only, no device work)."""
+    import json
+    from paper_1802_10291_gb300 import mci
+    src = tmp_path / "in.json"
+    entries = {"generic-1d|fp32|real|P=768|T=2304|Min=1|Q=3|Test GPU|sm=4": 5,
+               "generic-1d|fp64|complex|P=96|T=384|Min=2|Q=8|Test GPU|sm=4": 12}
+    src.write_text(json.dumps(entries, indent=1))
+    mci.mci_tune_cache_load(str(src))
+    out = tmp_path / "out.json"
+    mci.mci_tune_cache_save(str(out))
+    saved = json.loads(out.read_text())
+    for k, v in entries.items():
+        assert saved[k] == v
+    for bad in ('{"k": 0}', '{"k": 65}', '{"k" 3}', 'not json', '{"k": 3'):
+        f = tmp_path / "bad.json"
+        f.write_text(bad)
+        with pytest.raises(mci.MciError) as e:
+            mci.mci_tune_cache_load(str(f))
+        assert e.value.status == mci.MCI_ERR_INVALID_ARG
+    with pytest.raises(mci.MciError):
+        mci.mci_tune_cache_load(str(tmp_path / "missing.json"))

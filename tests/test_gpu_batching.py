@@ -116,3 +116,59 @@ def test_host_buffers_pipeline(cuda_device, pinned, access):
     assert plan.info()["device_status"] == 0
     assert torch.equal(y, ref.cpu())
     plan.close()
+
+
+def test_refused_allocations_return_oom_and_free(cuda_device):
+    """Every allocation of plan creation refused in turn (test hook): MCI_ERR_OOM, nothing
+    leaked on the device, and the first plan that gets all its memory works."""
+    from paper_1802_10291_gb300 import mci as M
+    systems = [("identity",), ("hilbert",), ("deriv", 1)]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    refused = 0
+    try:
+        for k in range(32):
+            M.mci_debug_fail_allocation(k)
+            try:
+                plan = M.Plan(systems, [256, 512], [1024, 2048], max_batch=64)
+            except M.MciError as e:
+                assert e.status == M.MCI_ERR_OOM, e.status
+                refused += 1
+                continue
+            break
+    finally:
+        M.mci_debug_fail_allocation(-1)
+    assert refused >= 3
+    x = torch.randn((5, 3, 256), device="cuda")
+    y = torch.empty((5, 1, 1024), device="cuda")
+    M.mci_interp_1d(plan.handle, x, None, y, None, np.zeros(5, np.int32), 5)
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0 and torch.isfinite(y).all()
+    plan.close()
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= 64 << 20
+
+
+def test_autotune_cache_reused_and_saved(cuda_device, tmp_path):
+    """A second autotuned plan with the same classes takes the tile heights from the cache
+    (no timing: much faster plan creation, same heights); save / load round-trips them."""
+    import json
+    import time
+    systems = [("identity",), ("deriv", 1)]
+    Ps, Ts = [96, 192, 384], [288, 576, 1152]    # generic-kernel classes (3 x 2^a)
+    t0 = time.perf_counter()
+    a = mci.Plan(systems, Ps, Ts, max_batch=64, autotune=True)
+    t1 = time.perf_counter()
+    b = mci.Plan(systems, Ps, Ts, max_batch=64, autotune=True)
+    t2 = time.perf_counter()
+    ga, gb = a.info()["signals_per_cta"][:3], b.info()["signals_per_cta"][:3]
+    assert ga == gb
+    assert t2 - t1 < 0.5 * (t1 - t0)
+    path = tmp_path / "tune.json"
+    mci.mci_tune_cache_save(str(path))
+    saved = json.loads(path.read_text())
+    keys = [k for k in saved if "|P=384|T=1152|" in k]
+    assert keys and saved[keys[0]] == ga[2]
+    mci.mci_tune_cache_load(str(path))
+    a.close()
+    b.close()
