@@ -140,13 +140,25 @@ struct FastTile {
     const C* tab;            // the class's fused-path table
     const float* in;
     float* out;
-    const int64_t* s_in;     // per signal of the tile (shared memory)
-    const int64_t* s_out;
+    const int64_t* s_in;     // per signal of the tile (shared memory); image columns: the
+    const int64_t* s_out;    // offsets of their first samples, consecutive columns
     int cnt;                 // signals in the tile
+    int64_t ld;              // image columns: the row pitch of input and output (else 0)
 };
 
+// Image columns: the G = 2048/N columns of a tile are staged through shared memory so that
+// every global access is a row segment of the G columns.  Column g's words start rotated by
+// (32/G) g, which keeps the row-wise staging accesses and the column-wise FFT accesses free of
+// bank conflicts (G columns x 32/G rows of a warp cover the 32 banks).
+template <int N>
+__device__ __forceinline__ int col_rot(int g)
+{
+    return (32 / (2048 / N)) * g;
+}
+
 // The whole pipeline for one tile (all threads of the CTA; smem_raw holds the buffers).
-template <int N, int MIN, int S, int NOUT>
+// COLS: the signals are G consecutive image columns (one channel, one output).
+template <int N, int MIN, int S, int NOUT, bool COLS = false>
 __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* smem_raw)
 {
     constexpr int Q = S * NOUT, QM = MIN > Q ? MIN : Q;
@@ -175,7 +187,29 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
         C x[MIN][8];
         const float* src = ft.in + (active ? ft.s_in[g] : 0);
         const bool al = (reinterpret_cast<uintptr_t>(src) & 7) == 0;
-        if (active && al) {
+        if constexpr (COLS) {
+            static_assert(MIN == 1 && NOUT == 1 && S >= 2, "image columns: one channel, one output");
+            // rows p of the tile's columns into buffer 1 of each column (rotated), g fastest
+            constexpr int G = 2048 / N;
+            const float* base = ft.in + ft.s_in[0];
+#pragma unroll 8
+            for (int it = tid; it < P * G; it += 256) {
+                const int pp = it / G, gg = it - pp * G;
+                const float v = gg < ft.cnt ? __ldcs(base + gg + (int64_t)pp * ft.ld) : 0.f;
+                reinterpret_cast<float*>(reinterpret_cast<C*>(smem_raw) + gg * QM * N + N)[(pp + col_rot<N>(gg)) & (P - 1)] = v;
+            }
+            __syncthreads();
+            const float* st = reinterpret_cast<const float*>(sm + N);
+            const int rot = col_rot<N>(g);
+#pragma unroll
+            for (int i = 0; i < P0::NB; ++i)
+#pragma unroll
+                for (int r = 0; r < P0::R; ++r) {
+                    const float2 z = *reinterpret_cast<const float2*>(
+                        st + ((2 * (jn + TPS * i + r * P0::ST) + rot) & (P - 1)));
+                    x[0][i * P0::R + r] = mk<float>(z.x, z.y);
+                }
+        } else if (active && al) {
 #pragma unroll
             for (int m = 0; m < MIN; ++m)
 #pragma unroll
@@ -281,6 +315,44 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
         C y[Q][8];
         PL::template load<Q>(sm, jn, y);
         PL::template compute<Q>(y, jn, tab);
+        if constexpr (COLS) {
+            // samples [2 S l, 2 S l + 2 S) of the column (re of phases 0..S-1, then im) into the
+            // column's buffers as T = 2 S N floats, rotated, then rows of the G columns out
+            constexpr int G = 2048 / N;
+            __syncthreads();   // every thread has read its last-pass inputs
+            float* oc = reinterpret_cast<float*>(sm);
+            const int rot = col_rot<N>(g);
+#pragma unroll
+            for (int i = 0; i < PL::NB; ++i)
+#pragma unroll
+                for (int r = 0; r < PL::R; ++r) {
+                    const int l = jn + TPS * i + r * PL::ST, e = i * PL::R + r;
+                    float v[2 * S];
+#pragma unroll
+                    for (int u = 0; u < S; ++u) {
+                        v[u] = y[u][e].x;
+                        v[S + u] = y[u][e].y;
+                    }
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        int pos = 2 * S * l + 2 * k + rot;
+                        if (pos >= T) pos -= T;
+                        *reinterpret_cast<float2*>(oc + pos) = make_float2(v[2 * k], v[2 * k + 1]);
+                    }
+                }
+            __syncthreads();
+            float* obase = ft.out + ft.s_out[0];
+#pragma unroll 8
+            for (int it = tid; it < T * G; it += 256) {
+                const int xr = it / G, gg = it - xr * G;
+                int pos = xr + col_rot<N>(gg);
+                if (pos >= T) pos -= T;
+                if (gg < ft.cnt)
+                    __stcs(obase + gg + (int64_t)xr * ft.ld, reinterpret_cast<const float*>(
+                                                              reinterpret_cast<C*>(smem_raw) + gg * QM * N)[pos]);
+            }
+            return;
+        }
         // all lanes take part in the shuffles below; only active signals store
         float* dst0 = ft.out + (active ? ft.s_out[g] : 0);
         // element l of phase buffer (o, u) holds samples s (2l) + u (real part) and
@@ -350,10 +422,41 @@ __global__ void __launch_bounds__(256, 2) mci_fast_kernel(const KArgs a)
                                smem_raw);
 }
 
+// One CTA per tile of G = 2048/N consecutive columns of one image's intermediate (the column
+// pass of the separable 2-D path): item (image, tile) of the class's column list.
+template <int N, int MIN, int S, int NOUT>
+__global__ void __launch_bounds__(256, 2) mci_fast_cols_kernel(const KArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int64_t s_in[kMaxTile];
+    __shared__ int64_t s_out[kMaxTile];
+    constexpr int G = 2048 / N;
+    const int2 it = a.items[a.sched2->col_start[a.cls] + blockIdx.x];
+    const int i = it.x;
+    const int64_t ld = (int64_t)a.scale[i] * a.w[i];   // intermediate and HR row pitch
+    const int64_t c0 = (int64_t)it.y * G;
+    const int cnt = (int)min((int64_t)G, ld - c0);
+    if (threadIdx.x == 0) {
+        s_in[0] = a.inter_off[i] + c0;
+        s_out[0] = a.img_out_off[i] + c0;
+    }
+    __syncthreads();
+    const C* W = static_cast<const C*>(a.W);
+    fast_tile<N, MIN, S, NOUT, true>(FastTile{W, W + a.c.tw_rel, static_cast<const float*>(a.in),
+                                              static_cast<float*>(a.out), s_in, s_out, cnt, ld},
+                                     smem_raw);
+}
+
 }  // namespace
 
+// Fused variants (index, N, input channels, scale, outputs).  The first kFastPersistentVariants
+// (the batched 1-D workload's classes) are also compiled into the persistent kernel.
 #define MCI_FAST_VARIANTS(X) \
     X(0, 128, 3, 4, 1) X(1, 256, 3, 4, 1) X(2, 512, 3, 4, 1) X(3, 1024, 3, 4, 1) X(4, 2048, 3, 4, 1)
+// image rows and columns: one channel (the derivative channels folded into the weights)
+#define MCI_FAST_IMG_VARIANTS(X)                                                                \
+    X(5, 128, 1, 2, 1) X(6, 256, 1, 2, 1) X(7, 512, 1, 2, 1) X(8, 128, 1, 3, 1) X(9, 256, 1, 3, 1) \
+    X(10, 512, 1, 3, 1) X(11, 128, 1, 4, 1) X(12, 256, 1, 4, 1) X(13, 512, 1, 4, 1)
 
 namespace {
 
@@ -429,7 +532,17 @@ const void* fast_kernel_lookup(int N, int M_in, int s, int n_out, int* variant)
         return (const void*)mci_fast_kernel<n, m, sc, no>;           \
     }
     MCI_FAST_VARIANTS(MCI_FAST_CASE)
+    MCI_FAST_IMG_VARIANTS(MCI_FAST_CASE)
 #undef MCI_FAST_CASE
+    return nullptr;
+}
+
+const void* fast_cols_kernel_lookup(int N, int M_in, int s, int n_out)
+{
+#define MCI_FAST_CCASE(v, n, m, sc, no) \
+    if (N == n && M_in == m && s == sc && n_out == no) return (const void*)mci_fast_cols_kernel<n, m, sc, no>;
+    MCI_FAST_IMG_VARIANTS(MCI_FAST_CCASE)
+#undef MCI_FAST_CCASE
     return nullptr;
 }
 
@@ -444,7 +557,20 @@ __device__ bool device_launch_fast(const ClassDev& c, int grid, int smem, const 
         return true;                                                                          \
     }
     MCI_FAST_VARIANTS(MCI_FAST_DCASE)
+    MCI_FAST_IMG_VARIANTS(MCI_FAST_DCASE)
 #undef MCI_FAST_DCASE
+    return false;
+}
+
+__device__ bool device_launch_fast_cols(const ClassDev& c, int grid, int smem, const KArgs& a)
+{
+#define MCI_FAST_DCCASE(v, n, m, sc, no)                                                      \
+    if (c.N == n && c.M_in == m && c.s == sc && c.n_out == no) {                               \
+        mci_fast_cols_kernel<n, m, sc, no><<<grid, 256, smem, cudaStreamFireAndForget>>>(a);   \
+        return true;                                                                          \
+    }
+    MCI_FAST_IMG_VARIANTS(MCI_FAST_DCCASE)
+#undef MCI_FAST_DCCASE
     return false;
 }
 

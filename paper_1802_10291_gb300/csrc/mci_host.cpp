@@ -1062,10 +1062,14 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         cd_.out_len = (int64_t)cd_.n_out * hc.T * (d.complex_signal ? 2 : 1);
         // fused radix-8 kernel: real FP32 1-D classes with N a power of two in its range and a
         // compiled (channels, scale, outputs) variant; its tile and shared memory are fixed
+        // image plans: rows and columns both on the fused path (one tile height for both
+        // passes), N up to kFastMaxImageN, where a column variant is compiled
         int var = -1;
-        cd_.fast = d.precision == MCI_FP32 && !d.complex_signal && d.max_images == 0 &&
-                           hc.N >= kFastMinN && hc.N <= kFastMaxN && (hc.N & (hc.N - 1)) == 0 &&
-                           fast_kernel_lookup(hc.N, cd_.M_in, hc.s, p->n_out, &var) != nullptr
+        const bool img = d.max_images > 0;
+        cd_.fast = d.precision == MCI_FP32 && !d.complex_signal && hc.N >= kFastMinN &&
+                           hc.N <= (img ? kFastMaxImageN : kFastMaxN) && (hc.N & (hc.N - 1)) == 0 &&
+                           fast_kernel_lookup(hc.N, cd_.M_in, hc.s, p->n_out, &var) != nullptr &&
+                           (!img || fast_cols_kernel_lookup(hc.N, cd_.M_in, hc.s, p->n_out) != nullptr)
                        ? 1 + var
                        : 0;
         if (cd_.fast) continue;
@@ -1139,7 +1143,10 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         L.smem = p->csmem[c];
         p->kern[c] = p->cdev[c].fast ? fast_kernel_lookup(p->cdev[c].N, p->cdev[c].M_in, p->cdev[c].s, p->n_out)
                                      : kernel_lookup(d.precision, false, p->cdev[c].N);
-        p->kern_cols[c] = d.precision == MCI_FP32 ? kernel_lookup(d.precision, true, p->cdev[c].N) : nullptr;
+        p->kern_cols[c] = d.precision != MCI_FP32 ? nullptr
+                          : p->cdev[c].fast ? fast_cols_kernel_lookup(p->cdev[c].N, p->cdev[c].M_in, p->cdev[c].s, p->n_out)
+                                            : kernel_lookup(d.precision, true, p->cdev[c].N);
+        if (p->cdev[c].fast && d.max_images > 0 && !p->kern_cols[c]) e = cudaErrorInvalidDeviceFunction;
         if (!p->kern[c]) e = cudaErrorInvalidDeviceFunction;
         // The dynamic shared-memory limit is an attribute of the kernel function, which
         // size classes of one FFT length (in this plan or another) share: it is set to
@@ -1155,7 +1162,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             // those, the rest of the SM's storage to L1 (the bin weights and twiddles are read
             // through it; measured 10% faster than the largest carveout); others: largest
             int carve = cudaSharedmemCarveoutMaxShared;
-            if (k == p->kern[c] && p->cdev[c].fast) {
+            if (p->cdev[c].fast) {
                 const int need = 2 * (p->csmem[c] + (int)fa.sharedSizeBytes + 1024);
                 carve = std::min(100, (100 * need + (int)prop.sharedMemPerMultiprocessor - 1) /
                                           (int)prop.sharedMemPerMultiprocessor);
@@ -1166,7 +1173,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     // uneven batches whose classes are all on the fused path: one persistent launch
     p->persist = n > 1 && fast_persistent_kernel() != nullptr;
     for (int c = 0; c < n; ++c) {
-        p->persist = p->persist && p->cdev[c].fast;
+        p->persist = p->persist && p->cdev[c].fast >= 1 && p->cdev[c].fast <= kFastPersistentVariants;
         p->persist_smem = std::max(p->persist_smem, p->csmem[c]);
     }
     if (e == cudaSuccess && p->persist) {

@@ -224,6 +224,11 @@ const void* kernel_lookup(int precision, bool cols, int N);
 // Fused radix-8 kernel for (N, input channels, scale, outputs), or NULL when not compiled;
 // *variant (if not NULL) receives its index in the persistent kernel's dispatch.
 const void* fast_kernel_lookup(int N, int M_in, int s, int n_out, int* variant = nullptr);
+// Its column-pass counterpart for image plans (separable 2-D), or NULL.
+const void* fast_cols_kernel_lookup(int N, int M_in, int s, int n_out);
+// Variants 0 .. kFastPersistentVariants - 1 are the ones the persistent kernel dispatches.
+constexpr int kFastPersistentVariants = 5;
+constexpr int kFastMaxImageN = 512;   // image rows and columns on the fused path: N <= 512
 
 // One persistent launch over an uneven batch whose classes are all on the fused path: the
 // CTAs take tiles from sched->next_tile (zero at launch), classes in `order` (largest P

@@ -18,10 +18,11 @@ __device__ bool device_launch_d(int prec, bool cols, int N, int grid, int smem, 
 __device__ bool device_launch_e(int prec, bool cols, int N, int grid, int smem, const KArgs& a);
 
 __device__ bool device_launch_fast(const ClassDev& c, int grid, int smem, const KArgs& a);
+__device__ bool device_launch_fast_cols(const ClassDev& c, int grid, int smem, const KArgs& a);
 
 __device__ void launch_class(const ClassLaunch& L, bool cols, int grid, const KArgs& a, int* status)
 {
-    bool ok = (!cols && L.c.fast) ? device_launch_fast(L.c, grid, L.smem, a) :
+    bool ok = L.c.fast ? (cols ? device_launch_fast_cols(L.c, grid, L.smem, a) : device_launch_fast(L.c, grid, L.smem, a)) :
               device_launch_a(L.prec, cols, L.c.N, grid, L.smem, a) ||
               device_launch_b(L.prec, cols, L.c.N, grid, L.smem, a) ||
               device_launch_c(L.prec, cols, L.c.N, grid, L.smem, a) ||

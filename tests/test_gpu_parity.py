@@ -391,3 +391,46 @@ def test_few_signals_many_phases(cuda_device, prec, systems, P, s, batch):
     g = S.rng_for(1, 50 + P + s).standard_normal((batch, len(systems), P))
     out = run_1d(g, systems, s * P, prec, outputs=outs)
     check(out, O.mci_direct(systems, g, s * P, outputs=outs), prec)
+
+
+# (h, w, s): row class (w, s w) and column class (h, s h).  Power-of-two sides 256 .. 1024 run
+# on the fused kernels (rows and columns); 12 and 200-ish sides on the generic ones.  The last
+# image's 36 columns leave a ragged tile of the 16-column tiles of the (256, 768) class.
+_FUSED_2D = [(512, 512, 3), (1024, 256, 4), (256, 1024, 3), (512, 256, 2), (256, 12, 3)]
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_upsample_2d_fused_classes_match_oracle(cuda_device, where):
+    systems = [F, D1]
+    rng = S.rng_for(2, 11)
+    # the generator's blobs and edges need sides of 64 or more: the narrow image is uniform noise
+    imgs = [(S.synthetic_image(rng, h, w) if min(h, w) >= 64 else rng.random((h, w))).astype(np.float32)
+            for h, w, _ in _FUSED_2D]
+    PT = sorted({(w, s * w) for h, w, s in _FUSED_2D} | {(h, s * h) for h, w, s in _FUSED_2D})
+    plan = mci.Plan(systems, [p for p, _ in PT], [t for _, t in PT], channels="fd", max_batch=1,
+                    max_images=len(imgs), max_intermediate=sum(h * s * w for h, w, s in _FUSED_2D))
+    mask = plan.info()["fused_mask"]
+    for k, (p_, t_) in enumerate(PT):
+        assert bool(mask & (1 << k)) == (p_ in (256, 512, 1024)), (p_, t_)
+    lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), device="cuda")
+    n_hr = sum(s * s * h * w for h, w, s in _FUSED_2D)
+    hr = torch.full((n_hr,), float("nan"), device="cuda")
+    dev = "cuda" if where == "device" else "cpu"
+    hh = torch.tensor([h for h, _, _ in _FUSED_2D], dtype=torch.int32, device=dev)
+    ww = torch.tensor([w for _, w, _ in _FUSED_2D], dtype=torch.int32, device=dev)
+    ss = torch.tensor([s for _, _, s in _FUSED_2D], dtype=torch.int32, device=dev)
+    plan.upsample_2d(lr, hh, ww, ss, hr, len(imgs))
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    out = hr.cpu().double().numpy()
+    assert np.all(np.isfinite(out))
+    pos = 0
+    crng = S.rng_for(2, 12)
+    for (h, w, s), im in zip(_FUSED_2D, imgs):
+        Wd = s * w
+        cols = np.unique(np.r_[0, 1, 15, 16, 17, Wd // 2, Wd - 3, Wd - 2, Wd - 1, crng.integers(0, Wd, 3)])
+        cols = cols[cols < Wd]
+        got = out[pos:pos + s * h * Wd].reshape(s * h, Wd)[:, cols]
+        pos += s * h * Wd
+        check(got, _oracle_columns(im, s, systems, cols), "fp32")
+    plan.close()
