@@ -118,19 +118,31 @@ struct Pass {
     }
 };
 
+// Barrier among the N/8 threads of signal g of a tile.  Between the tile's loads and its
+// stores the signals share nothing, so each waits only for its own threads: its warp when it
+// fits in one, else named barrier 1 + g (barrier 0 stays the CTA-wide one).
+template <int N>
+__device__ __forceinline__ void sig_sync(int g)
+{
+    constexpr int TPS = N / 8;
+    if constexpr (TPS >= 256) __syncthreads();
+    else if constexpr (TPS <= 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(TPS) : "memory");
+}
+
 // Passes PS .. L-2 of a transform, each: load, barrier, twiddles and DFTs, store, barrier.
 template <int N, int V, int PS, bool INV>
-__device__ __forceinline__ void middle_passes(C* sm, int j, const C* tab)
+__device__ __forceinline__ void middle_passes(C* sm, int j, const C* tab, int g)
 {
     if constexpr (PS < fast_passes(N) - 1) {
         using PP = Pass<N, PS, INV>;
         C v[V][8];
         PP::template load<V>(sm, j, v);
-        __syncthreads();
+        sig_sync<N>(g);
         PP::template compute<V>(v, j, tab);
         PP::template store<V>(sm, j, v);
-        __syncthreads();
-        middle_passes<N, V, PS + 1, INV>(sm, j, tab);
+        sig_sync<N>(g);
+        middle_passes<N, V, PS + 1, INV>(sm, j, tab, g);
     }
 }
 
@@ -237,9 +249,9 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
         }
         P0::template compute<MIN>(x, jn, tab);
         P0::template store<MIN>(sm, jn, x);
-        __syncthreads();
+        sig_sync<N>(g);
     }
-    middle_passes<N, MIN, 1, false>(sm, jn, tab);
+    middle_passes<N, MIN, 1, false>(sm, jn, tab, g);
 
     // ---- last forward pass (permuted index), spectra, combine, first inverse pass ----
     {
@@ -247,7 +259,7 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
         static_assert(PL::R == 8, "the last forward pass is radix 8");
         C z[MIN][8];
         PL::template load<MIN>(sm, jm, z);
-        __syncthreads();   // the first inverse pass below overwrites these buffers
+        sig_sync<N>(g);   // the first inverse pass below overwrites these buffers
         PL::template compute<MIN>(z, jm, tab);
         // z[m][r] = Z_m[k], k = jm + TPS r; its mirror N - k is element 7 - r of the partner
         // lane, except on the two self-paired lanes: jm = 0 (k = TPS r <-> TPS (8 - r)) and
@@ -305,9 +317,9 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
 #pragma unroll
             for (int r = 0; r < 8; ++r) sm[q * N + swz<1, 8>(8 * jm + r)] = zp[r];
         }
-        __syncthreads();
+        sig_sync<N>(g);
     }
-    middle_passes<N, Q, 1, true>(sm, jn, tab);
+    middle_passes<N, Q, 1, true>(sm, jn, tab, g);
 
     // ---- last inverse pass, output samples straight to global memory ----
     {
@@ -333,11 +345,22 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
                         v[u] = y[u][e].x;
                         v[S + u] = y[u][e].y;
                     }
+                    if constexpr (S % 2 == 0 && N >= 256) {
+                        // the rotation (4 g or 8 g words) keeps the 2S-word chunks 16-byte aligned
 #pragma unroll
-                    for (int k = 0; k < S; ++k) {
-                        int pos = 2 * S * l + 2 * k + rot;
-                        if (pos >= T) pos -= T;
-                        *reinterpret_cast<float2*>(oc + pos) = make_float2(v[2 * k], v[2 * k + 1]);
+                        for (int k = 0; k < S / 2; ++k) {
+                            int pos = 2 * S * l + 4 * k + rot;
+                            if (pos >= T) pos -= T;
+                            *reinterpret_cast<float4*>(oc + pos) =
+                                make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < S; ++k) {
+                            int pos = 2 * S * l + 2 * k + rot;
+                            if (pos >= T) pos -= T;
+                            *reinterpret_cast<float2*>(oc + pos) = make_float2(v[2 * k], v[2 * k + 1]);
+                        }
                     }
                 }
             __syncthreads();
