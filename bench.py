@@ -612,7 +612,7 @@ def main():
     ap.add_argument("--pairs", type=int, default=20000,
                     help="corrector_train case: training pairs (batches of 4, one step each)")
     ap.add_argument("--case", default=None,
-                    choices=["kernel4096", "corrector", "corrector_train", "corrector_small", "sisr_s4",
+                    choices=["kernel4096", "corrector", "corrector_train", "corrector_small", "sisr_s2", "sisr_s4",
                              "uneven2d", "images", "mci2d"],
                     help="profiling case: the P=4096 size-class kernel alone on 3277 signals")
     args = ap.parse_args()
@@ -713,18 +713,21 @@ def main():
         out = uneven_2d_section(mci, torch, dev, timed, args.steps)
         print(json.dumps({"case": args.case, **out}), flush=True)
         return
-    if args.case == "sisr_s4":
-        # profiling case: 64 synthetic 512^2 images from x4 decimation (tensor-core path)
+    if args.case in ("sisr_s2", "sisr_s4"):
+        # profiling cases: 64 synthetic 512^2 images from x2 (FFT path) or x4 decimation
+        # (tensor-core path)
         from paper_1802_10291_gb300 import synth
+        s_ = 2 if args.case == "sisr_s2" else 4
+        L = 512 // s_
         rng = synth.rng_for(2, 0)
         hr_np = np.stack([synth.synthetic_image(rng, 512) for _ in range(64)]).astype(np.float32)
-        lr_np = synth.decimate(hr_np, 4)
-        plan = mci.Plan([("identity",), ("deriv", 1)], 128, 512, channels="fd", max_batch=1,
-                        max_images=64, max_intermediate=64 * 128 * 512)
+        lr_np = synth.decimate(hr_np, s_)
+        plan = mci.Plan([("identity",), ("deriv", 1)], L, 512, channels="fd", max_batch=1,
+                        max_images=64, max_intermediate=64 * L * 512)
         lr = torch.tensor(lr_np.reshape(-1), device=dev)
         hr = torch.empty(64 * 512 * 512, device=dev)
-        hh = np.full(64, 128, np.int32)
-        ss = np.full(64, 4, np.int32)
+        hh = np.full(64, L, np.int32)
+        ss = np.full(64, s_, np.int32)
         t, _ = timed(lambda: plan.upsample_2d(lr, hh, hh, ss, hr, 64), args.steps, args.warmup)
         print(json.dumps({"case": args.case, "ms_per_batch": 1e3 * t / args.steps}), flush=True)
         return

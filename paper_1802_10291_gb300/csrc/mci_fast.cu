@@ -201,14 +201,23 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
         const bool al = (reinterpret_cast<uintptr_t>(src) & 7) == 0;
         if constexpr (COLS) {
             static_assert(MIN == 1 && NOUT == 1 && S >= 2, "image columns: one channel, one output");
-            // rows p of the tile's columns into buffer 1 of each column (rotated), g fastest
-            constexpr int G = 2048 / N;
-            const float* base = ft.in + ft.s_in[0];
-#pragma unroll 8
-            for (int it = tid; it < P * G; it += 256) {
-                const int pp = it / G, gg = it - pp * G;
-                const float v = gg < ft.cnt ? __ldcs(base + gg + (int64_t)pp * ft.ld) : 0.f;
-                reinterpret_cast<float*>(reinterpret_cast<C*>(smem_raw) + gg * QM * N + N)[(pp + col_rot<N>(gg)) & (P - 1)] = v;
+            // rows p of the tile's columns into buffer 1 of each column (rotated): thread tid
+            // stages column tid mod G, rows tid / G + (256 / G) k, k < P G / 256 = 16
+            constexpr int G = 2048 / N, RPI = 256 / G;
+            const int gs = tid % G, p0 = tid / G;
+            float* dstc = reinterpret_cast<float*>(reinterpret_cast<C*>(smem_raw) + gs * QM * N + N);
+            const int q0 = p0 + col_rot<N>(gs);
+            if (gs < ft.cnt) {
+                const float* src = ft.in + ft.s_in[0] + gs + (int64_t)p0 * ft.ld;
+                const int64_t step = (int64_t)RPI * ft.ld;
+#pragma unroll
+                for (int k = 0; k < P / RPI; ++k) {
+                    dstc[(q0 + RPI * k) & (P - 1)] = __ldcs(src);
+                    src += step;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < P / RPI; ++k) dstc[(q0 + RPI * k) & (P - 1)] = 0.f;
             }
             __syncthreads();
             const float* st = reinterpret_cast<const float*>(sm + N);
@@ -364,15 +373,21 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
                     }
                 }
             __syncthreads();
-            float* obase = ft.out + ft.s_out[0];
+            // rows x of the tile's columns out: thread tid writes column tid mod G, rows
+            // tid / G + (256 / G) k, k < T G / 256 = 16 S
+            const int gs = tid % G, x0 = tid / G;
+            if (gs < ft.cnt) {
+                const float* srcc = reinterpret_cast<const float*>(reinterpret_cast<C*>(smem_raw) + gs * QM * N);
+                float* dst = ft.out + ft.s_out[0] + gs + (int64_t)x0 * ft.ld;
+                const int64_t step = (int64_t)(256 / G) * ft.ld;
+                int pos = x0 + col_rot<N>(gs);   // < 256 / G + 32 <= T
 #pragma unroll 8
-            for (int it = tid; it < T * G; it += 256) {
-                const int xr = it / G, gg = it - xr * G;
-                int pos = xr + col_rot<N>(gg);
-                if (pos >= T) pos -= T;
-                if (gg < ft.cnt)
-                    __stcs(obase + gg + (int64_t)xr * ft.ld, reinterpret_cast<const float*>(
-                                                              reinterpret_cast<C*>(smem_raw) + gg * QM * N)[pos]);
+                for (int k = 0; k < T / (256 / G); ++k) {
+                    __stcs(dst, srcc[pos]);
+                    dst += step;
+                    pos += 256 / G;
+                    if (pos >= T) pos -= T;
+                }
             }
             return;
         }
