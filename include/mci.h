@@ -179,6 +179,8 @@ typedef struct {
     unsigned fused_mask;     /* bit c: size class c runs on the fused radix-8 kernel      */
     int persistent_ctas;     /* grid of the one persistent launch that serves uneven
                                 batches when every class is fused (0: one launch per class) */
+    unsigned fused3_mask;    /* bit c: the image columns of size class c (N = 3 N') run on
+                                the fused factor-3 column kernel                            */
 } mci_plan_stats;
 
 /*

@@ -562,6 +562,249 @@ __global__ void __launch_bounds__(256, 2) mci_fast_persistent(const PersistArgs 
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Image columns with a factor 3: N = 3 N' (P = 6 N'), N' a power of two, one channel, one
+// output, s phases.  The length-N packed transform is split by decimation in time into the
+// three sub-sequences z[3 n + n1], whose length-N' transforms run as three vectors on the
+// radix-8 passes above (N'/8 threads per column); a radix-3 step in registers combines them:
+//   Z[k1 + N' k2] = sum_n1 e^{-2 pi i n1 k1 / N} e^{-2 pi i n1 k2 / 3} F_n1[k1].
+// The inverse of each phase is the transpose: a radix-3 step (decimation in frequency, with
+// the conjugate twiddles) and three inverse length-N' transforms, whose element n2 of
+// sub-transform n1 is the complex sample n1 + 3 n2.  The mirror bins N - k of the real
+// spectra are exchanged through shared memory in natural bin order.  The phases are produced
+// one after another from the channel spectrum held in registers, so a column needs N complex
+// values of shared memory: its staged input, the sub-transform buffers and one phase's
+// output in turn.  G = 2048 / N' columns per CTA, staged as in the radix-8 column kernel.
+// ---------------------------------------------------------------------------------------
+template <int NQ, int S>
+__global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int N = 3 * NQ, P = 2 * N, TPS = NQ / 8, G = 2048 / NQ, L = fast_passes(NQ);
+    constexpr int RPI = 256 / G;   // rows per staging step
+    static_assert(NQ >= kFastMinN && (NQ & (NQ - 1)) == 0 && (P * G) % 256 == 0, "factor-3 column class");
+    const int2 item = a.items[a.sched2->col_start[a.cls] + blockIdx.x];
+    const int img = item.x;
+    const int64_t ld = (int64_t)a.scale[img] * a.w[img];   // intermediate and HR row pitch
+    const int64_t c0 = (int64_t)item.y * G;
+    const int cnt = (int)min((int64_t)G, ld - c0);
+    const float* in = static_cast<const float*>(a.in) + a.inter_off[img] + c0;
+    float* out = static_cast<float*>(a.out) + a.img_out_off[img] + c0;
+    const C* W = static_cast<const C*>(a.W);
+    const C* tab = W + a.c.tw_rel;                                  // e^{-2 pi i k / P}, k <= N
+    const C* ptab = tab + (N + 1) - (NQ + 1);                      // pass twiddles (length N')
+    const C* tw3 = tab + (N + 1) + fast_tw_count(NQ) - (NQ + 1);   // e^{-2 pi i k / N}, k < N'
+    const int tid = threadIdx.x, g = tid / TPS, j = tid - g * TPS;
+    C* sm = reinterpret_cast<C*>(smem_raw) + g * N;
+    const int rot = col_rot<NQ>(g);
+
+    // ---- rows p < P of the G columns into their buffers, rotated by col_rot words ----
+    {
+        const int gs = tid % G, p0 = tid / G;
+        float* dstc = reinterpret_cast<float*>(reinterpret_cast<C*>(smem_raw) + gs * N);
+        int q = p0 + col_rot<NQ>(gs);
+        if (gs < cnt) {
+            const float* src = in + gs + (int64_t)p0 * ld;
+            const int64_t step = (int64_t)RPI * ld;
+#pragma unroll 8
+            for (int k = 0; k < P / RPI; ++k) {
+                dstc[q] = __ldcs(src);
+                src += step;
+                q += RPI;
+                if (q >= P) q -= P;
+            }
+        } else {
+#pragma unroll 8
+            for (int k = 0; k < P / RPI; ++k) {
+                dstc[q] = 0.f;
+                q += RPI;
+                if (q >= P) q -= P;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- forward pass 0 of the sub-transforms: sub-sequence n1 is z[3 n + n1] ----
+    {
+        using P0 = Pass<NQ, 0, false>;
+        C x[3][8];
+        const float* st = reinterpret_cast<const float*>(sm);
+#pragma unroll
+        for (int n1 = 0; n1 < 3; ++n1)
+#pragma unroll
+            for (int i = 0; i < P0::NB; ++i)
+#pragma unroll
+                for (int r = 0; r < P0::R; ++r) {
+                    int pos = 6 * (j + TPS * i + r * P0::ST) + 2 * n1 + rot;
+                    if (pos >= P) pos -= P;
+                    const float2 v = *reinterpret_cast<const float2*>(st + pos);
+                    x[n1][i * P0::R + r] = mk<float>(v.x, v.y);
+                }
+        sig_sync<NQ>(g);   // the staged column is read before pass 0 overwrites it
+        P0::template compute<3>(x, j, ptab);
+        P0::template store<3>(sm, j, x);
+        sig_sync<NQ>(g);
+    }
+    middle_passes<NQ, 3, 1, false>(sm, j, ptab, g);
+
+    // ---- last forward pass and the radix-3 step: z[k2][r] = Z[k1 + N' k2], k1 = j + TPS r ----
+    C z[3][8];
+    {
+        using PL = Pass<NQ, L - 1, false>;
+        static_assert(PL::R == 8, "the last forward pass is radix 8");
+        PL::template load<3>(sm, j, z);
+        PL::template compute<3>(z, j, ptab);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const C w1 = ldc(tw3 + j + TPS * r), w2 = cmul(w1, w1);
+            C v[3] = {z[0][r], cmul(z[1][r], w1), cmul(z[2][r], w2)};
+            dft<3, false>(v);
+            z[0][r] = v[0];
+            z[1][r] = v[1];
+            z[2][r] = v[2];
+        }
+    }
+    // ---- real-input spectrum X[k] = (Z[k] + conj Z[N-k]) / 2 + e^{-2 pi i k / P} (Z[k] - conj Z[N-k]) / (2i)
+    const float xN = z[0][0].x - z[0][0].y;   // X[N] (real), on the j = 0 lane
+    sig_sync<NQ>(g);   // the last pass has read the sub-transform buffers
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sm[j + TPS * r + NQ * k2] = z[k2][r];
+    sig_sync<NQ>(g);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int k = j + TPS * r + NQ * k2;
+            const C zm = sm[k == 0 ? 0 : N - k];
+            const C e = scale(z[k2][r] + conjc(zm), 0.5f);
+            const C d = z[k2][r] - conjc(zm);
+            z[k2][r] = e + cmul(ldc(tab + k), mk<float>(0.5f * d.y, -0.5f * d.x));
+        }
+
+    // ---- output phases u < s, one at a time ----
+#pragma unroll 1
+    for (int u = 0; u < S; ++u) {
+        // phase spectrum Y_u[k] = X[k] W_u[k] (Eq. (matrixeqn1) through the folded weights)
+        const C* Wu = W + (size_t)u * (N + 1);
+        C y[3][8];
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) y[k2][r] = cmul(z[k2][r], ldc(Wu + j + TPS * r + NQ * k2));
+        const C yN = scale(ldc(Wu + N), xN);   // Y_u[N], used on the j = 0 lane
+        sig_sync<NQ>(g);   // earlier reads of the column buffer are done
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) sm[j + TPS * r + NQ * k2] = y[k2][r];
+        sig_sync<NQ>(g);
+        // packing for the real inverse FFT: A + i C, A = Y[k] + conj Y[N-k],
+        // C = e^{2 pi i k / P} (Y[k] - conj Y[N-k])
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int k = j + TPS * r + NQ * k2;
+                const C ym = k == 0 ? yN : sm[N - k];
+                const C A = y[k2][r] + conjc(ym);
+                const C Cc = cmulc(y[k2][r] - conjc(ym), ldc(tab + k));
+                y[k2][r] = mk<float>(A.x - Cc.y, A.y + Cc.x);
+            }
+        // radix-3 step of the inverse: G_n1[k1] = e^{2 pi i n1 k1 / N} sum_k2 Zp[k1 + N' k2] e^{2 pi i n1 k2 / 3},
+        // then inverse pass 0 (stride 1) of sub-transform n1: butterfly j writes element r at 8 j + r
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const C w1 = ldc(tw3 + j + TPS * r), w2 = cmul(w1, w1);
+            C v[3] = {y[0][r], y[1][r], y[2][r]};
+            dft<3, true>(v);
+            y[0][r] = v[0];
+            y[1][r] = cmulc(v[1], w1);
+            y[2][r] = cmulc(v[2], w2);
+        }
+#pragma unroll
+        for (int n1 = 0; n1 < 3; ++n1) dft<8, true>(y[n1]);
+        sig_sync<NQ>(g);   // every lane has read its mirror bins
+#pragma unroll
+        for (int n1 = 0; n1 < 3; ++n1)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) sm[n1 * NQ + swz<1, 8>(8 * j + r)] = y[n1][r];
+        sig_sync<NQ>(g);
+        middle_passes<NQ, 3, 1, true>(sm, j, ptab, g);
+        // last inverse pass: element n2 = j + TPS i + r ST of sub-transform n1 is the complex
+        // sample n1 + 3 n2, i.e. the real samples m = 2 (n1 + 3 n2) and m + 1 of phase u,
+        // staged at word m + rot (mod P) of the column buffer
+        {
+            using PL = Pass<NQ, L - 1, true>;
+            PL::template load<3>(sm, j, y);
+            PL::template compute<3>(y, j, ptab);
+            sig_sync<NQ>(g);
+            float* oc = reinterpret_cast<float*>(sm);
+#pragma unroll
+            for (int n1 = 0; n1 < 3; ++n1)
+#pragma unroll
+                for (int i = 0; i < PL::NB; ++i)
+#pragma unroll
+                    for (int r = 0; r < PL::R; ++r) {
+                        int pos = 2 * (n1 + 3 * (j + TPS * i + r * PL::ST)) + rot;
+                        if (pos >= P) pos -= P;
+                        const C v = y[n1][i * PL::R + r];
+                        *reinterpret_cast<float2*>(oc + pos) = make_float2(v.x, v.y);
+                    }
+        }
+        __syncthreads();
+        // HR rows s m + u, m < P, of the G columns: thread tid writes column tid mod G,
+        // m = tid / G + RPI k
+        {
+            const int gs = tid % G, m0 = tid / G;
+            if (gs < cnt) {
+                const float* srcc = reinterpret_cast<const float*>(reinterpret_cast<C*>(smem_raw) + gs * N);
+                float* dst = out + gs + ((int64_t)S * m0 + u) * ld;
+                const int64_t step = (int64_t)S * RPI * ld;
+                int q = m0 + col_rot<NQ>(gs);
+#pragma unroll 8
+                for (int k = 0; k < P / RPI; ++k) {
+                    __stcs(dst, srcc[q]);
+                    dst += step;
+                    q += RPI;
+                    if (q >= P) q -= P;
+                }
+            }
+        }
+        __syncthreads();   // the buffers are free for the next phase
+    }
+}
+
+}  // namespace
+
+// Factor-3 column variants (N', s).
+#define MCI_FAST3_VARIANTS(X) X(128, 2) X(128, 3) X(128, 4)
+
+const void* fast3_cols_kernel_lookup(int N, int M_in, int s, int n_out)
+{
+    if (M_in != 1 || n_out != 1 || N % 3 != 0) return nullptr;
+#define MCI_FAST3_CASE(nq, sc) \
+    if (N == 3 * nq && s == sc) return (const void*)mci_fast3_cols_kernel<nq, sc>;
+    MCI_FAST3_VARIANTS(MCI_FAST3_CASE)
+#undef MCI_FAST3_CASE
+    return nullptr;
+}
+
+__device__ bool device_launch_fast3_cols(const ClassDev& c, int grid, int smem, const KArgs& a)
+{
+#define MCI_FAST3_DCASE(nq, sc)                                                             \
+    if (c.N == 3 * nq && c.s == sc) {                                                       \
+        mci_fast3_cols_kernel<nq, sc><<<grid, 256, smem, cudaStreamFireAndForget>>>(a);     \
+        return true;                                                                        \
+    }
+    MCI_FAST3_VARIANTS(MCI_FAST3_DCASE)
+#undef MCI_FAST3_DCASE
+    return false;
+}
+
 const void* fast_kernel_lookup(int N, int M_in, int s, int n_out, int* variant)
 {
 #define MCI_FAST_CASE(v, n, m, sc, no)                              \

@@ -249,6 +249,7 @@ struct mci_plan_s {
     std::vector<const void*> kern;    // per class host kernel (contiguous pattern)
     std::vector<const void*> kern_cols;
     std::vector<int> csmem;           // per class dynamic shared memory
+    std::vector<int> csmem_cols;      // per class dynamic shared memory of the column kernel
     int n_sm = 0;                     // multiprocessors of the plan's device
     int persist = 0;                  // uneven batches: one persistent launch (all classes fused)
     int persist_ctas = 0;             // its grid: resident CTAs per SM x SMs
@@ -560,6 +561,20 @@ mci_status build_tables(mci_plan_s* p, std::vector<R>& W)
                     for (int jm = 0; jm < ns; ++jm) push_cpx(W, cis_frac(-(int64_t)jm, (int64_t)ns * rad));
                 }
         }
+        if (cd_.fast3) {
+            // factor-3 column table: e^{-2 pi i k / P}, k = 0..N; the per-pass twiddles of the
+            // length-N' transforms (N' = N / 3); e^{-2 pi i k / N}, k < N'
+            const int Nq = N / 3;
+            if ((W.size() / 2) % 2) push_cpx(W, cd(0.0));
+            cd_.tw_rel = (int)((int64_t)(W.size() / 2) - cd_.w_off);
+            for (int k = 0; k <= N; ++k) push_cpx(W, cis_frac(-(int64_t)k, P));
+            for (int inv = 0; inv < 2; ++inv)
+                for (int ps = 1; ps < fast_passes(Nq); ++ps) {
+                    const int ns = fast_ns(Nq, inv, ps), rad = fast_radix(Nq, inv, ps);
+                    for (int jm = 0; jm < ns; ++jm) push_cpx(W, cis_frac(-(int64_t)jm, (int64_t)ns * rad));
+                }
+            for (int k = 0; k < Nq; ++k) push_cpx(W, cis_frac(-(int64_t)k, N));
+        }
         if (gemm) {
             // out[s l + u] = sum_p kappa_u[(l - p) mod P] x[p], kappa_u[d] = sum over all P bins of
             // W_k[u] e^{2 pi i k d / P} with W_{P-k} = conj W_k (the kernel's real inverse FFT)
@@ -697,7 +712,7 @@ static cudaError_t launch_classes(mci_plan_t p, const KArgs& tmpl, bool cols, co
         e = cudaStreamWaitEvent(p->cstreams[c], p->ev_fork, 0);
         if (e == cudaSuccess)
             e = cudaLaunchKernel(k, dim3((unsigned)counts[c]), dim3(kThreads), args,
-                                 (size_t)p->csmem[c], p->cstreams[c]);
+                                 (size_t)(cols ? p->csmem_cols[c] : p->csmem[c]), p->cstreams[c]);
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_join[c], p->cstreams[c]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[c], 0);
     }
@@ -778,7 +793,7 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
             ++n_gemm;
         } else {
             rcnt[rc[i]] += (hi + p->cdev[rc[i]].G - 1) / p->cdev[rc[i]].G;
-            ccnt[cc[i]] += (int)(((int64_t)si * wi + p->cdev[cc[i]].G - 1) / p->cdev[cc[i]].G);
+            ccnt[cc[i]] += (int)(((int64_t)si * wi + p->cdev[cc[i]].Gc - 1) / p->cdev[cc[i]].Gc);
         }
         inter_off[i] = inter;
         lr_pref[i] = lr;
@@ -811,7 +826,7 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
     for (int64_t i = 0; i < n_img; ++i) {
         if (by_gemm[i]) continue;
         const int nr = (h[i] + p->cdev[rc[i]].G - 1) / p->cdev[rc[i]].G;
-        const int nc = (int)(((int64_t)scale[i] * w[i] + p->cdev[cc[i]].G - 1) / p->cdev[cc[i]].G);
+        const int nc = (int)(((int64_t)scale[i] * w[i] + p->cdev[cc[i]].Gc - 1) / p->cdev[cc[i]].Gc);
         for (int t = 0; t < nr; ++t) items[rcur[rc[i]]++] = make_int2((int)i, t);
         for (int t = 0; t < nc; ++t) items[ccur[cc[i]]++] = make_int2((int)i, t);
     }
@@ -992,9 +1007,14 @@ static cudaError_t autotune_tiles(mci_plan_s* p, int smem_cap, cudaStream_t s)
     if (e == cudaSuccess) {
         p->smem = 0;
         for (int c = 0; c < n; ++c) {
+            if (!p->cdev[c].fast3) {   // columns share the rows' tile
+                p->cdev[c].Gc = p->cdev[c].G;
+                p->csmem_cols[c] = p->csmem[c];
+            }
             p->smem = std::max(p->smem, p->csmem[c]);
             p->launch[c].c = p->cdev[c];
             p->launch[c].smem = p->csmem[c];
+            p->launch[c].smem_cols = p->csmem_cols[c];
         }
         e = cudaMemcpyAsync(p->d_launch, p->launch.data(), sizeof(ClassLaunch) * n, cudaMemcpyHostToDevice, s);
     }
@@ -1072,6 +1092,10 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
                            (!img || fast_cols_kernel_lookup(hc.N, cd_.M_in, hc.s, p->n_out) != nullptr)
                        ? 1 + var
                        : 0;
+        // image columns of a class with N = 3 N' (N' a power of two): the fused factor-3 column
+        // kernel (its own tile of 2048 / N' columns); the rows stay on the generic kernel
+        cd_.fast3 = !cd_.fast && img && d.precision == MCI_FP32 && !d.complex_signal &&
+                    fast3_cols_kernel_lookup(hc.N, cd_.M_in, hc.s, p->n_out) != nullptr;
         if (cd_.fast) continue;
         const int per = cd_.sstride * csz + smem_twiddle_count(hc.N) * csz;
         if (per > smem_cap) {
@@ -1082,11 +1106,12 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
     }
     const int budget = std::max(need, std::min(kSmemBudget, smem_cap));
     p->csmem.resize(n);
+    p->csmem_cols.resize(n);
     for (int c = 0; c < n; ++c) {
         ClassDev& cd_ = p->cdev[c];
         if (cd_.fast) {   // 2048 / N signals of QM buffers of N complex values
-            cd_.G = 2048 / cd_.N;
-            p->csmem[c] = cd_.G * cd_.QM * cd_.N * csz;
+            cd_.G = cd_.Gc = 2048 / cd_.N;
+            p->csmem[c] = p->csmem_cols[c] = cd_.G * cd_.QM * cd_.N * csz;
             p->smem = std::max(p->smem, p->csmem[c]);
             continue;
         }
@@ -1099,6 +1124,13 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             return MCI_ERR_UNSUPPORTED_SIZE;
         }
         p->smem = std::max(p->smem, p->csmem[c]);
+        cd_.Gc = cd_.G;
+        p->csmem_cols[c] = p->csmem[c];
+        if (cd_.fast3) {   // 2048 / N' columns of N complex values
+            cd_.Gc = 2048 / (cd_.N / 3);
+            p->csmem_cols[c] = cd_.Gc * cd_.N * csz;
+            p->smem = std::max(p->smem, p->csmem_cols[c]);
+        }
     }
     p->order.resize(n);
     for (int c = 0; c < n; ++c) p->order[c] = c;
@@ -1141,11 +1173,13 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         L.W = (const char*)p->d_W + p->cdev[c].w_off * 2 * p->elem;
         L.prec = d.precision;
         L.smem = p->csmem[c];
+        L.smem_cols = p->csmem_cols[c];
         p->kern[c] = p->cdev[c].fast ? fast_kernel_lookup(p->cdev[c].N, p->cdev[c].M_in, p->cdev[c].s, p->n_out)
                                      : kernel_lookup(d.precision, false, p->cdev[c].N);
         p->kern_cols[c] = d.precision != MCI_FP32 ? nullptr
                           : p->cdev[c].fast ? fast_cols_kernel_lookup(p->cdev[c].N, p->cdev[c].M_in, p->cdev[c].s, p->n_out)
-                                            : kernel_lookup(d.precision, true, p->cdev[c].N);
+                          : p->cdev[c].fast3 ? fast3_cols_kernel_lookup(p->cdev[c].N, p->cdev[c].M_in, p->cdev[c].s, p->n_out)
+                                             : kernel_lookup(d.precision, true, p->cdev[c].N);
         if (p->cdev[c].fast && d.max_images > 0 && !p->kern_cols[c]) e = cudaErrorInvalidDeviceFunction;
         if (!p->kern[c]) e = cudaErrorInvalidDeviceFunction;
         // The dynamic shared-memory limit is an attribute of the kernel function, which
@@ -1162,8 +1196,8 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             // those, the rest of the SM's storage to L1 (the bin weights and twiddles are read
             // through it; measured 10% faster than the largest carveout); others: largest
             int carve = cudaSharedmemCarveoutMaxShared;
-            if (p->cdev[c].fast) {
-                const int need = 2 * (p->csmem[c] + (int)fa.sharedSizeBytes + 1024);
+            if (p->cdev[c].fast || (p->cdev[c].fast3 && k == p->kern_cols[c])) {
+                const int need = 2 * ((k == p->kern_cols[c] ? p->csmem_cols[c] : p->csmem[c]) + (int)fa.sharedSizeBytes + 1024);
                 carve = std::min(100, (100 * need + (int)prop.sharedMemPerMultiprocessor - 1) /
                                           (int)prop.sharedMemPerMultiprocessor);
             }
@@ -1471,6 +1505,8 @@ mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)
     st->workspace_bytes = p->work_bytes;
     for (size_t c = 0; c < p->cdev.size(); ++c)
         if (p->cdev[c].fast) st->fused_mask |= 1u << c;
+    for (size_t c = 0; c < p->cdev.size(); ++c)
+        if (p->cdev[c].fast3) st->fused3_mask |= 1u << c;
     st->persistent_ctas = p->persist ? p->persist_ctas : 0;
     cudaError_t e = cudaStreamSynchronize(p->last_stream);
     int status = 0;

@@ -124,6 +124,8 @@ struct ClassDev {
     int64_t out_len;     // reals per signal: n_out * T (x 2 for complex signals)
     int fast;            // fused radix-8 kernel (mci_fast.cu): 1 + its variant index, or 0
     int tw_rel;          // fused path: offset (complex) of the class table after its weights
+    int fast3;           // image columns on the fused factor-3 kernel (N = 3 N'), else 0
+    int Gc;              // signals per column tile (G, or the factor-3 kernel's 2048 / N')
 };
 
 // Grouping of one mci_interp_1d call (uneven batches), built on the device or on the host.
@@ -139,6 +141,7 @@ struct ClassLaunch {
     const void* W;
     int prec;
     int smem;
+    int smem_cols;   // dynamic shared memory of the class's column kernel
 };
 
 enum StatusBits {
@@ -228,6 +231,12 @@ const void* fast_kernel_lookup(int N, int M_in, int s, int n_out, int* variant =
 const void* fast_cols_kernel_lookup(int N, int M_in, int s, int n_out);
 // Variants 0 .. kFastPersistentVariants - 1 are the ones the persistent kernel dispatches.
 constexpr int kFastPersistentVariants = 5;
+// Image columns of length P = 6 N' (N = 3 N', N' a power of two) on the fused factor-3
+// kernel: its table layout after the class weights is e^{-2 pi i k / P} (k = 0..N), the
+// per-pass twiddles of the length-N' transforms (as fast_tw_offset(N', ..) lays them out
+// after N' + 1 entries), then e^{-2 pi i k / N} for k < N'.
+const void* fast3_cols_kernel_lookup(int N, int M_in, int s, int n_out);
+MCI_HD constexpr int fast3_table_count(int Nq) { return 3 * Nq + 1 + fast_tw_count(Nq) - (Nq + 1) + Nq; }
 constexpr int kFastMaxImageN = 512;   // image rows and columns on the fused path: N <= 512
 
 // One persistent launch over an uneven batch whose classes are all on the fused path: the

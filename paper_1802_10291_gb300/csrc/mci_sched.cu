@@ -19,15 +19,18 @@ __device__ bool device_launch_e(int prec, bool cols, int N, int grid, int smem, 
 
 __device__ bool device_launch_fast(const ClassDev& c, int grid, int smem, const KArgs& a);
 __device__ bool device_launch_fast_cols(const ClassDev& c, int grid, int smem, const KArgs& a);
+__device__ bool device_launch_fast3_cols(const ClassDev& c, int grid, int smem, const KArgs& a);
 
 __device__ void launch_class(const ClassLaunch& L, bool cols, int grid, const KArgs& a, int* status)
 {
-    bool ok = L.c.fast ? (cols ? device_launch_fast_cols(L.c, grid, L.smem, a) : device_launch_fast(L.c, grid, L.smem, a)) :
-              device_launch_a(L.prec, cols, L.c.N, grid, L.smem, a) ||
-              device_launch_b(L.prec, cols, L.c.N, grid, L.smem, a) ||
-              device_launch_c(L.prec, cols, L.c.N, grid, L.smem, a) ||
-              device_launch_d(L.prec, cols, L.c.N, grid, L.smem, a) ||
-              device_launch_e(L.prec, cols, L.c.N, grid, L.smem, a);
+    const int sm = cols ? L.smem_cols : L.smem;
+    bool ok = L.c.fast ? (cols ? device_launch_fast_cols(L.c, grid, sm, a) : device_launch_fast(L.c, grid, sm, a)) :
+              cols && L.c.fast3 ? device_launch_fast3_cols(L.c, grid, sm, a) :
+              device_launch_a(L.prec, cols, L.c.N, grid, sm, a) ||
+              device_launch_b(L.prec, cols, L.c.N, grid, sm, a) ||
+              device_launch_c(L.prec, cols, L.c.N, grid, sm, a) ||
+              device_launch_d(L.prec, cols, L.c.N, grid, sm, a) ||
+              device_launch_e(L.prec, cols, L.c.N, grid, sm, a);
     if (!ok || cudaGetLastError() != cudaSuccess) atomicOr(status, kStatusLaunch);
 }
 
@@ -199,7 +202,7 @@ sched_2d_kernel(int64_t n_img, int n_classes, const ClassLaunch* __restrict__ cl
             } else {
                 inter = (int64_t)hi * si * wi;
                 atomicAdd(&rcnt[rc], (hi + cl[rc].c.G - 1) / cl[rc].c.G);
-                atomicAdd(&ccnt[cc], (int)(((int64_t)si * wi + cl[cc].c.G - 1) / cl[cc].c.G));
+                atomicAdd(&ccnt[cc], (int)(((int64_t)si * wi + cl[cc].c.Gc - 1) / cl[cc].c.Gc));
             }
             row_cls[i] = rc;
             col_cls[i] = cc;
@@ -244,7 +247,7 @@ sched_2d_kernel(int64_t n_img, int n_classes, const ClassLaunch* __restrict__ cl
             const int rc = row_cls[i], cc = col_cls[i];
             if (rc < 0) continue;
             const int nr = (h[i] + cl[rc].c.G - 1) / cl[rc].c.G;
-            const int nc = (int)(((int64_t)scale[i] * w[i] + cl[cc].c.G - 1) / cl[cc].c.G);
+            const int nc = (int)(((int64_t)scale[i] * w[i] + cl[cc].c.Gc - 1) / cl[cc].c.Gc);
             int p = atomicAdd(&rcur[rc], nr);
             for (int t = 0; t < nr; ++t) items[p + t] = make_int2((int)i, t);
             p = atomicAdd(&ccur[cc], nc);

@@ -71,7 +71,8 @@ class mci_plan_stats(ctypes.Structure):
                 ("device_status", ctypes.c_int), ("signals_per_cta", ctypes.c_int * MCI_MAX_SIZES),
                 ("threads_per_cta", ctypes.c_int), ("smem_bytes", ctypes.c_int),
                 ("table_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("fused_mask", ctypes.c_uint), ("persistent_ctas", ctypes.c_int)]
+                ("fused_mask", ctypes.c_uint), ("persistent_ctas", ctypes.c_int),
+                ("fused3_mask", ctypes.c_uint)]
 
 
 _lib = None
@@ -287,7 +288,8 @@ def mci_plan_info(plan: int) -> dict:
             "device_status": st.device_status, "signals_per_cta": list(st.signals_per_cta),
             "threads_per_cta": st.threads_per_cta, "smem_bytes": st.smem_bytes,
             "table_bytes": st.table_bytes, "workspace_bytes": st.workspace_bytes,
-            "fused_mask": st.fused_mask, "persistent_ctas": st.persistent_ctas}
+            "fused_mask": st.fused_mask, "persistent_ctas": st.persistent_ctas,
+            "fused3_mask": st.fused3_mask}
 
 
 def mci_destroy(plan: int):

@@ -434,3 +434,44 @@ def test_upsample_2d_fused_classes_match_oracle(cuda_device, where):
         pos += s * h * Wd
         check(got, _oracle_columns(im, s, systems, cols), "fp32")
     plan.close()
+
+
+# images 768 high: columns of P = 768 = 6 N' (N' = 128) on the fused factor-3 column kernel,
+# s = 2, 3, 4; widths give full tiles of 16 columns and a ragged last tile (s w = 36)
+_FACTOR3_2D = [(768, 64, 2), (768, 48, 3), (768, 96, 4), (768, 12, 3)]
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_upsample_2d_factor3_columns_match_oracle(cuda_device, where):
+    systems = [F, D1]
+    rng = S.rng_for(2, 13)
+    imgs = [(S.synthetic_image(rng, h, w) if min(h, w) >= 64 else rng.random((h, w))).astype(np.float32)
+            for h, w, _ in _FACTOR3_2D]
+    PT = sorted({(w, s * w) for h, w, s in _FACTOR3_2D} | {(h, s * h) for h, w, s in _FACTOR3_2D})
+    plan = mci.Plan(systems, [p for p, _ in PT], [t for _, t in PT], channels="fd", max_batch=1,
+                    max_images=len(imgs), max_intermediate=sum(h * s * w for h, w, s in _FACTOR3_2D))
+    mask3 = plan.info()["fused3_mask"]
+    for k, (p_, t_) in enumerate(PT):
+        assert bool(mask3 & (1 << k)) == (p_ == 768), (p_, t_)
+    lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), device="cuda")
+    n_hr = sum(s * s * h * w for h, w, s in _FACTOR3_2D)
+    hr = torch.full((n_hr,), float("nan"), device="cuda")
+    dev = "cuda" if where == "device" else "cpu"
+    hh = torch.tensor([h for h, _, _ in _FACTOR3_2D], dtype=torch.int32, device=dev)
+    ww = torch.tensor([w for _, w, _ in _FACTOR3_2D], dtype=torch.int32, device=dev)
+    ss = torch.tensor([s for _, _, s in _FACTOR3_2D], dtype=torch.int32, device=dev)
+    plan.upsample_2d(lr, hh, ww, ss, hr, len(imgs))
+    torch.cuda.synchronize()
+    assert plan.info()["device_status"] == 0
+    out = hr.cpu().double().numpy()
+    assert np.all(np.isfinite(out))
+    pos = 0
+    crng = S.rng_for(2, 14)
+    for (h, w, s), im in zip(_FACTOR3_2D, imgs):
+        Wd = s * w
+        cols = np.unique(np.r_[0, 1, 15, 16, 17, Wd // 2, Wd - 3, Wd - 2, Wd - 1, crng.integers(0, Wd, 3)])
+        cols = cols[cols < Wd]
+        got = out[pos:pos + s * h * Wd].reshape(s * h, Wd)[:, cols]
+        pos += s * h * Wd
+        check(got, _oracle_columns(im, s, systems, cols), "fp32")
+    plan.close()
