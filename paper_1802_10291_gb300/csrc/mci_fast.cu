@@ -72,8 +72,9 @@ struct Pass {
     static constexpr int ST = N / R;
 
     // element (i, r) of thread j: butterfly j + TPS i, input r
+    // fx: XORed into every element index (a per-signal layout; 0 on the radix-8 kernels)
     template <int V>
-    static __device__ __forceinline__ void load(const C* sm, int j, C (&v)[V][8])
+    static __device__ __forceinline__ void load(const C* sm, int j, C (&v)[V][8], int fx = 0)
     {
         constexpr int PNS = fast_ns(N, INV, PS - 1), PR = fast_radix(N, INV, PS - 1);
 #pragma unroll
@@ -81,7 +82,7 @@ struct Pass {
 #pragma unroll
             for (int i = 0; i < NB; ++i)
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[x][i * R + r] = sm[x * N + swz<PNS, PR>(j + TPS * i + r * ST)];
+                for (int r = 0; r < R; ++r) v[x][i * R + r] = sm[x * N + (swz<PNS, PR>(j + TPS * i + r * ST) ^ fx)];
     }
 
     template <int V>
@@ -104,7 +105,7 @@ struct Pass {
     }
 
     template <int V>
-    static __device__ __forceinline__ void store(C* sm, int j, const C (&v)[V][8])
+    static __device__ __forceinline__ void store(C* sm, int j, const C (&v)[V][8], int fx = 0)
     {
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
@@ -113,7 +114,7 @@ struct Pass {
 #pragma unroll
             for (int x = 0; x < V; ++x)
 #pragma unroll
-                for (int r = 0; r < R; ++r) sm[x * N + swz<NS, R>(d + r * NS)] = v[x][i * R + r];
+                for (int r = 0; r < R; ++r) sm[x * N + (swz<NS, R>(d + r * NS) ^ fx)] = v[x][i * R + r];
         }
     }
 };
@@ -132,17 +133,17 @@ __device__ __forceinline__ void sig_sync(int g)
 
 // Passes PS .. L-2 of a transform, each: load, barrier, twiddles and DFTs, store, barrier.
 template <int N, int V, int PS, bool INV>
-__device__ __forceinline__ void middle_passes(C* sm, int j, const C* tab, int g)
+__device__ __forceinline__ void middle_passes(C* sm, int j, const C* tab, int g, int fx = 0)
 {
     if constexpr (PS < fast_passes(N) - 1) {
         using PP = Pass<N, PS, INV>;
         C v[V][8];
-        PP::template load<V>(sm, j, v);
+        PP::template load<V>(sm, j, v, fx);
         sig_sync<N>(g);
         PP::template compute<V>(v, j, tab);
-        PP::template store<V>(sm, j, v);
+        PP::template store<V>(sm, j, v, fx);
         sig_sync<N>(g);
-        middle_passes<N, V, PS + 1, INV>(sm, j, tab, g);
+        middle_passes<N, V, PS + 1, INV>(sm, j, tab, g, fx);
     }
 }
 
@@ -577,14 +578,35 @@ namespace {
 // one after another from the channel spectrum held in registers, so a column needs N complex
 // values of shared memory: its staged input, the sub-transform buffers and one phase's
 // output in turn.  G = 2048 / N' columns per CTA, staged as in the radix-8 column kernel.
+// With N' = 64 (8 threads per column) two columns share each half warp; then the odd column
+// of a pair stores its sub-transform buffers with the element index XOR 12 and its spectra
+// with XOR 8, its staged words rotated by 16 more, and a warp stages 16 columns x 2 rows,
+// which keeps every access of the pair free of bank conflicts.
 // ---------------------------------------------------------------------------------------
+
+// Staged-word rotation of column g, and the staging thread map (column, first row; rows step
+// by 256 / G).
+template <int NQ>
+__device__ __forceinline__ int rot3(int g)
+{
+    if constexpr (NQ / 8 >= 16) return col_rot<NQ>(g);
+    else return (16 * (g & 1) + 2 * (g >> 1)) & 31;
+}
+template <int NQ>
+__device__ __forceinline__ int2 stage3(int t)
+{
+    constexpr int G = 2048 / NQ;
+    if constexpr (G <= 16) return make_int2(t % G, t / G);
+    else return make_int2((t & 15) + 16 * ((t >> 5) & 1), 2 * (t >> 6) + ((t >> 4) & 1));
+}
+
 template <int NQ, int S>
 __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int N = 3 * NQ, P = 2 * N, TPS = NQ / 8, G = 2048 / NQ, L = fast_passes(NQ);
     constexpr int RPI = 256 / G;   // rows per staging step
-    static_assert(NQ >= kFastMinN && (NQ & (NQ - 1)) == 0 && (P * G) % 256 == 0, "factor-3 column class");
+    static_assert(NQ >= 64 && NQ <= 256 && (NQ & (NQ - 1)) == 0 && (P * G) % 256 == 0, "factor-3 column class");
     const int2 item = a.items[a.sched2->col_start[a.cls] + blockIdx.x];
     const int img = item.x;
     const int64_t ld = (int64_t)a.scale[img] * a.w[img];   // intermediate and HR row pitch
@@ -598,13 +620,16 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
     const C* tw3 = tab + (N + 1) + fast_tw_count(NQ) - (NQ + 1);   // e^{-2 pi i k / N}, k < N'
     const int tid = threadIdx.x, g = tid / TPS, j = tid - g * TPS;
     C* sm = reinterpret_cast<C*>(smem_raw) + g * N;
-    const int rot = col_rot<NQ>(g);
+    const int rot = rot3<NQ>(g);
+    const bool odd = TPS < 16 && (g & 1);
+    const int fx = odd ? 12 : 0, sx = odd ? 8 : 0;   // per-column index XORs (see above)
 
     // ---- rows p < P of the G columns into their buffers, rotated by col_rot words ----
     {
-        const int gs = tid % G, p0 = tid / G;
+        const int2 m = stage3<NQ>(tid);
+        const int gs = m.x, p0 = m.y;
         float* dstc = reinterpret_cast<float*>(reinterpret_cast<C*>(smem_raw) + gs * N);
-        int q = p0 + col_rot<NQ>(gs);
+        int q = p0 + rot3<NQ>(gs);
         if (gs < cnt) {
             const float* src = in + gs + (int64_t)p0 * ld;
             const int64_t step = (int64_t)RPI * ld;
@@ -644,17 +669,17 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
                 }
         sig_sync<NQ>(g);   // the staged column is read before pass 0 overwrites it
         P0::template compute<3>(x, j, ptab);
-        P0::template store<3>(sm, j, x);
+        P0::template store<3>(sm, j, x, fx);
         sig_sync<NQ>(g);
     }
-    middle_passes<NQ, 3, 1, false>(sm, j, ptab, g);
+    middle_passes<NQ, 3, 1, false>(sm, j, ptab, g, fx);
 
     // ---- last forward pass and the radix-3 step: z[k2][r] = Z[k1 + N' k2], k1 = j + TPS r ----
     C z[3][8];
     {
         using PL = Pass<NQ, L - 1, false>;
         static_assert(PL::R == 8, "the last forward pass is radix 8");
-        PL::template load<3>(sm, j, z);
+        PL::template load<3>(sm, j, z, fx);
         PL::template compute<3>(z, j, ptab);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -672,14 +697,14 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
 #pragma unroll
     for (int k2 = 0; k2 < 3; ++k2)
 #pragma unroll
-        for (int r = 0; r < 8; ++r) sm[j + TPS * r + NQ * k2] = z[k2][r];
+        for (int r = 0; r < 8; ++r) sm[(j + TPS * r + NQ * k2) ^ sx] = z[k2][r];
     sig_sync<NQ>(g);
 #pragma unroll
     for (int k2 = 0; k2 < 3; ++k2)
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int k = j + TPS * r + NQ * k2;
-            const C zm = sm[k == 0 ? 0 : N - k];
+            const C zm = sm[(k == 0 ? 0 : N - k) ^ sx];
             const C e = scale(z[k2][r] + conjc(zm), 0.5f);
             const C d = z[k2][r] - conjc(zm);
             z[k2][r] = e + cmul(ldc(tab + k), mk<float>(0.5f * d.y, -0.5f * d.x));
@@ -700,7 +725,7 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
 #pragma unroll
         for (int k2 = 0; k2 < 3; ++k2)
 #pragma unroll
-            for (int r = 0; r < 8; ++r) sm[j + TPS * r + NQ * k2] = y[k2][r];
+            for (int r = 0; r < 8; ++r) sm[(j + TPS * r + NQ * k2) ^ sx] = y[k2][r];
         sig_sync<NQ>(g);
         // packing for the real inverse FFT: A + i C, A = Y[k] + conj Y[N-k],
         // C = e^{2 pi i k / P} (Y[k] - conj Y[N-k])
@@ -709,7 +734,7 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const int k = j + TPS * r + NQ * k2;
-                const C ym = k == 0 ? yN : sm[N - k];
+                const C ym = k == 0 ? yN : sm[(N - k) ^ sx];
                 const C A = y[k2][r] + conjc(ym);
                 const C Cc = cmulc(y[k2][r] - conjc(ym), ldc(tab + k));
                 y[k2][r] = mk<float>(A.x - Cc.y, A.y + Cc.x);
@@ -731,15 +756,15 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
 #pragma unroll
         for (int n1 = 0; n1 < 3; ++n1)
 #pragma unroll
-            for (int r = 0; r < 8; ++r) sm[n1 * NQ + swz<1, 8>(8 * j + r)] = y[n1][r];
+            for (int r = 0; r < 8; ++r) sm[n1 * NQ + (swz<1, 8>(8 * j + r) ^ fx)] = y[n1][r];
         sig_sync<NQ>(g);
-        middle_passes<NQ, 3, 1, true>(sm, j, ptab, g);
+        middle_passes<NQ, 3, 1, true>(sm, j, ptab, g, fx);
         // last inverse pass: element n2 = j + TPS i + r ST of sub-transform n1 is the complex
         // sample n1 + 3 n2, i.e. the real samples m = 2 (n1 + 3 n2) and m + 1 of phase u,
         // staged at word m + rot (mod P) of the column buffer
         {
             using PL = Pass<NQ, L - 1, true>;
-            PL::template load<3>(sm, j, y);
+            PL::template load<3>(sm, j, y, fx);
             PL::template compute<3>(y, j, ptab);
             sig_sync<NQ>(g);
             float* oc = reinterpret_cast<float*>(sm);
@@ -759,12 +784,13 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
         // HR rows s m + u, m < P, of the G columns: thread tid writes column tid mod G,
         // m = tid / G + RPI k
         {
-            const int gs = tid % G, m0 = tid / G;
+            const int2 m = stage3<NQ>(tid);
+            const int gs = m.x, m0 = m.y;
             if (gs < cnt) {
                 const float* srcc = reinterpret_cast<const float*>(reinterpret_cast<C*>(smem_raw) + gs * N);
                 float* dst = out + gs + ((int64_t)S * m0 + u) * ld;
                 const int64_t step = (int64_t)S * RPI * ld;
-                int q = m0 + col_rot<NQ>(gs);
+                int q = m0 + rot3<NQ>(gs);
 #pragma unroll 8
                 for (int k = 0; k < P / RPI; ++k) {
                     __stcs(dst, srcc[q]);
@@ -781,7 +807,7 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
 }  // namespace
 
 // Factor-3 column variants (N', s).
-#define MCI_FAST3_VARIANTS(X) X(128, 2) X(128, 3) X(128, 4)
+#define MCI_FAST3_VARIANTS(X) X(64, 2) X(64, 3) X(64, 4) X(128, 2) X(128, 3) X(128, 4)
 
 const void* fast3_cols_kernel_lookup(int N, int M_in, int s, int n_out)
 {

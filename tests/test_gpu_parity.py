@@ -436,9 +436,11 @@ def test_upsample_2d_fused_classes_match_oracle(cuda_device, where):
     plan.close()
 
 
-# images 768 high: columns of P = 768 = 6 N' (N' = 128) on the fused factor-3 column kernel,
-# s = 2, 3, 4; widths give full tiles of 16 columns and a ragged last tile (s w = 36)
-_FACTOR3_2D = [(768, 64, 2), (768, 48, 3), (768, 96, 4), (768, 12, 3)]
+# images 768 and 384 high: columns of P = 6 N' (N' = 128: tiles of 16 columns; N' = 64: tiles
+# of 32, two columns per half warp) on the fused factor-3 column kernel, s = 2, 3, 4; widths
+# give full tiles and ragged last tiles (s w = 36, 72)
+_FACTOR3_2D = [(768, 64, 2), (768, 48, 3), (768, 96, 4), (768, 12, 3),
+               (384, 64, 2), (384, 24, 3), (384, 48, 4)]
 
 
 @pytest.mark.parametrize("where", ["host", "device"])
@@ -452,7 +454,7 @@ def test_upsample_2d_factor3_columns_match_oracle(cuda_device, where):
                     max_images=len(imgs), max_intermediate=sum(h * s * w for h, w, s in _FACTOR3_2D))
     mask3 = plan.info()["fused3_mask"]
     for k, (p_, t_) in enumerate(PT):
-        assert bool(mask3 & (1 << k)) == (p_ == 768), (p_, t_)
+        assert bool(mask3 & (1 << k)) == (p_ in (384, 768)), (p_, t_)
     lr = torch.tensor(np.concatenate([im.ravel() for im in imgs]), device="cuda")
     n_hr = sum(s * s * h * w for h, w, s in _FACTOR3_2D)
     hr = torch.full((n_hr,), float("nan"), device="cuda")
