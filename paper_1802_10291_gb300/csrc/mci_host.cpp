@@ -674,7 +674,11 @@ static mci_status interp_1d_host_grouped(mci_plan_t p, KArgs a, const int* size_
         if (e == cudaSuccess) e = launch_persistent(p, a, p->d_sorted, p->d_sched1, a.in_off, a.out_off, tiles, s);
         return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
+    // several non-empty classes run concurrently on their own streams (fork/join through
+    // events); a single one goes straight onto s (four API calls fewer)
+    int busy = 0;
+    for (int c = 0; c < n; ++c) busy += cnt[c] > 0;
+    if (e == cudaSuccess && busy > 1) e = cudaEventRecord(p->ev_fork, s);
     for (int oi = 0; oi < n && e == cudaSuccess; ++oi) {
         const int c = p->order[oi];
         if (cnt[c] == 0) continue;
@@ -684,23 +688,26 @@ static mci_status interp_1d_host_grouped(mci_plan_t p, KArgs a, const int* size_
         ac.cls = c;
         ac.W = p->launch[c].W;
         void* args[] = {&ac};
-        e = cudaStreamWaitEvent(p->cstreams[c], p->ev_fork, 0);
+        cudaStream_t cs = busy > 1 ? p->cstreams[c] : s;
+        if (busy > 1) e = cudaStreamWaitEvent(cs, p->ev_fork, 0);
         if (e == cudaSuccess)
-            e = cudaLaunchKernel(p->kern[c], dim3((unsigned)grid), dim3(kThreads), args,
-                                 (size_t)p->csmem[c], p->cstreams[c]);
-        if (e == cudaSuccess) e = cudaEventRecord(p->ev_join[c], p->cstreams[c]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[c], 0);
+            e = cudaLaunchKernel(p->kern[c], dim3((unsigned)grid), dim3(kThreads), args, (size_t)p->csmem[c], cs);
+        if (busy > 1 && e == cudaSuccess) e = cudaEventRecord(p->ev_join[c], cs);
+        if (busy > 1 && e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[c], 0);
     }
     return e == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
 }
 
 // Launch every non-empty class of one pass from the host, each on its own stream,
-// forked from and joined back into s.
+// forked from and joined back into s (a pass with one class: on s).
 static cudaError_t launch_classes(mci_plan_t p, const KArgs& tmpl, bool cols, const int* counts,
                                   cudaStream_t s)
 {
-    cudaError_t e = cudaEventRecord(p->ev_fork, s);
-    for (int oi = 0; oi < (int)p->cls.size() && e == cudaSuccess; ++oi) {
+    const int n = (int)p->cls.size();
+    int busy = 0;
+    for (int c = 0; c < n; ++c) busy += counts[c] > 0;
+    cudaError_t e = busy > 1 ? cudaEventRecord(p->ev_fork, s) : cudaSuccess;
+    for (int oi = 0; oi < n && e == cudaSuccess; ++oi) {
         const int c = p->order[oi];
         if (counts[c] == 0) continue;
         KArgs ac = tmpl;
@@ -709,12 +716,13 @@ static cudaError_t launch_classes(mci_plan_t p, const KArgs& tmpl, bool cols, co
         ac.W = p->launch[c].W;
         void* args[] = {&ac};
         const void* k = cols ? p->kern_cols[c] : p->kern[c];
-        e = cudaStreamWaitEvent(p->cstreams[c], p->ev_fork, 0);
+        cudaStream_t cs = busy > 1 ? p->cstreams[c] : s;   // a single class: straight onto s
+        if (busy > 1) e = cudaStreamWaitEvent(cs, p->ev_fork, 0);
         if (e == cudaSuccess)
             e = cudaLaunchKernel(k, dim3((unsigned)counts[c]), dim3(kThreads), args,
-                                 (size_t)(cols ? p->csmem_cols[c] : p->csmem[c]), p->cstreams[c]);
-        if (e == cudaSuccess) e = cudaEventRecord(p->ev_join[c], p->cstreams[c]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[c], 0);
+                                 (size_t)(cols ? p->csmem_cols[c] : p->csmem[c]), cs);
+        if (busy > 1 && e == cudaSuccess) e = cudaEventRecord(p->ev_join[c], cs);
+        if (busy > 1 && e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[c], 0);
     }
     return e;
 }
@@ -830,12 +838,9 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
         for (int t = 0; t < nr; ++t) items[rcur[rc[i]]++] = make_int2((int)i, t);
         for (int t = 0; t < nc; ++t) items[ccur[cc[i]]++] = make_int2((int)i, t);
     }
-    // upload the used part: offsets and the filled items, then the schedule and sizes
+    // upload the used part in one copy: offsets, schedule, sizes, GEMM jobs and the filled items
     const size_t head = p->o2_it + sizeof(int2) * (size_t)pos;
     cudaError_t e = cudaMemcpyAsync(p->d_inter_off, blk, head, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync((char*)p->d_inter_off + p->o2_s2, blk + p->o2_s2, p->stage2_bytes - p->o2_s2,
-                            cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev, s);
     p->stage2_cur ^= 1;
     for (KArgs* a : {&rows, &cols}) {
@@ -1271,13 +1276,14 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         o_ioff = carve(sizeof(int64_t) * I);
         o_lrp = carve(sizeof(int64_t) * I);
         o_hrp = carve(sizeof(int64_t) * I);
-        o_rc = carve(sizeof(int) * I);
-        o_cc = carve(sizeof(int) * I);
-        o_it = carve(sizeof(int2) * (size_t)p->max_items);
+        // the host-grouped path uploads [o_ioff, o_it + used items) in one copy
         o_s2 = carve(sizeof(Sched2D));
         o_hws = carve(sizeof(int) * 3 * I);
         o_jobs = carve(sizeof(GemmJob) * 2 * I);
         o_tile0 = carve(sizeof(int) * 2 * (I + 1));
+        o_rc = carve(sizeof(int) * I);
+        o_cc = carve(sizeof(int) * I);
+        o_it = carve(sizeof(int2) * (size_t)p->max_items);
     }
     if (e == cudaSuccess) e = dev_malloc((void**)&p->d_work, off);
     if (e != cudaSuccess) {
@@ -1324,7 +1330,7 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         }
     }
     if (I > 0 && e == cudaSuccess) {
-        p->stage2_bytes = o_tile0 + sizeof(int) * 2 * (I + 1) - o_ioff;
+        p->stage2_bytes = o_it + sizeof(int2) * (size_t)p->max_items - o_ioff;
         p->o2_jobs = o_jobs - o_ioff;
         p->o2_tile0 = o_tile0 - o_ioff;
         p->o2_lrp = o_lrp - o_ioff;
