@@ -305,6 +305,8 @@ struct mci_plan_s {
     std::vector<int64_t> gemm_off;
     std::vector<const float*> d_kmap;
     void* d_gemm = nullptr;
+    void* d_kplanes = nullptr;          // each class's K pre-split into BF16 plane tiles
+    std::vector<const char*> d_kp;
     GemmJob* d_jobs = nullptr;
     int* d_tile0 = nullptr;
     size_t o2_jobs = 0, o2_tile0 = 0;
@@ -770,6 +772,8 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
             r.A = (const float*)rows.in + (pack_lr ? lr : 0);
             r.a_off = pack_lr ? nullptr : rows.img_in_off;
             r.B = p->d_kmap[rc[i]];
+            r.a_planes = nullptr;
+            r.b_planes = p->d_kp[rc[i]];
             r.C = p->d_inter + inter;
             r.c_off = nullptr;
             r.lda = wi;
@@ -782,6 +786,8 @@ static mci_status upsample_2d_host_grouped(mci_plan_t p, KArgs rows, KArgs cols,
             r.transpose_c = 1;
             GemmJob& q = jobs[I + n_gemm];
             q.A = p->d_kmap[cc[i]];
+            q.a_planes = p->d_kp[cc[i]];
+            q.b_planes = nullptr;
             q.a_off = nullptr;
             q.B = p->d_inter + inter;
             q.C = (float*)cols.out + (pack_hr ? hrp : 0);
@@ -896,6 +902,7 @@ mci_status mci_destroy(mci_plan_t p)
     if (p->d_tables) cudaFree(p->d_tables);
     if (p->d_work) cudaFree(p->d_work);
     if (p->d_gemm) cudaFree(p->d_gemm);
+    if (p->d_kplanes) cudaFree(p->d_kplanes);
     if (p->d_rtab) cudaFree(p->d_rtab);
     if (p->d_chunk) cudaFree(p->d_chunk);
     for (cudaStream_t hs : p->hs)
@@ -1245,6 +1252,23 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
             if (p->gemm_off[c] >= 0) p->d_kmap[c] = (const float*)p->d_gemm + p->gemm_off[c];
         if (e == cudaSuccess) e = (cudaError_t)prepare_gemm();
         p->table_bytes += (int64_t)(sizeof(float) * p->gemm_tab.size());
+        // the constant operand of both GEMM passes, split once into the kernel's plane tiles
+        int64_t kp_bytes = 0;
+        std::vector<int64_t> kp_off(n, -1);
+        for (int c = 0; c < n; ++c)
+            if (p->gemm_off[c] >= 0) {
+                kp_off[c] = kp_bytes;
+                kp_bytes += gemm_plane_bytes(p->cls[c].T, p->cls[c].P);
+            }
+        if (e == cudaSuccess) e = dev_malloc(&p->d_kplanes, (size_t)kp_bytes);
+        p->d_kp.assign(n, nullptr);
+        for (int c = 0; c < n && e == cudaSuccess; ++c)
+            if (kp_off[c] >= 0) {
+                p->d_kp[c] = (const char*)p->d_kplanes + kp_off[c];
+                e = (cudaError_t)presplit_gemm(p->d_kmap[c], p->cls[c].T, p->cls[c].P,
+                                               (char*)p->d_kplanes + kp_off[c], s);
+            }
+        p->table_bytes += kp_bytes;
     }
 
     if (e == cudaSuccess && !p->rtab.empty()) {

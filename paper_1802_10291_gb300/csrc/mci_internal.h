@@ -166,6 +166,8 @@ struct GemmJob {
     int M, N, K;
     int img;
     int transpose_c;
+    const char* a_planes;    // A (or B) pre-split into BF16 plane tiles at plan time, or NULL
+    const char* b_planes;    // (at most one of the two)
 };
 
 // Device-built work lists of one mci_upsample_2d call: per size class, the
@@ -268,6 +270,9 @@ int launch_gemm(const GemmJob* jobs, const int* tile0, int n_jobs, int n_tiles, 
                 void* stream);
 int prepare_gemm();
 int gemm_smem_bytes();
+// Plane tiles of a constant rows x cols matrix (rows % 128 == 0, cols % 64 == 0).
+int64_t gemm_plane_bytes(int rows, int cols);
+int presplit_gemm(const float* K, int rows, int cols, char* out, void* stream);
 
 // Static scratch of mci_interp_1d_noalloc (mci_noalloc.cu).
 struct NoAllocScratch;
