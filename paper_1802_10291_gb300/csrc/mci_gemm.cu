@@ -13,7 +13,8 @@
 // made, into tiles of 128 rows x 64 columns laid out exactly as the kernel keeps them in
 // shared memory, and a tile's three planes arrive with one bulk asynchronous copy whose
 // bytes an mbarrier counts.  The other operand (the image or the intermediate) is read from
-// global memory and split by all threads.  K runs in chunks of 64 through one shared-memory
+// global memory and split by all threads, each chunk's loads issued before the previous
+// chunk's MMAs are waited for.  K runs in chunks of 64 through one shared-memory
 // stage, refilled once the MMAs that read it have committed; two CTAs share an SM (96 KB of
 // shared memory and at most 128 registers each), so one CTA's loads overlap the other's MMAs
 // and epilogue.  A row-major result goes out through the stage (free by then) so that each
@@ -81,19 +82,23 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// Load rows r0 .. r0 + 127, columns k0 .. k0 + 63 of a row-major FP32 operand and split them
-// into the three planes at dst: 2048 16-byte vectors, eight per thread, all loads in flight
-// before the first split.
-__device__ __forceinline__ void load_split(const float* X, int64_t ld, int r0, int k0, char* dst)
+// Rows r0 .. r0 + 127, columns k0 .. k0 + 63 of a row-major FP32 operand: 2048 16-byte
+// vectors, eight per thread, loaded into registers (all in flight at once) and then split
+// into the three planes at dst.
+constexpr int kPer = kTileM * (kChunkK / 4) / kGemmThreads;
+
+__device__ __forceinline__ void load_chunk(const float* X, int64_t ld, int r0, int k0, float4 (&v)[kPer])
 {
-    constexpr int kPer = kTileM * (kChunkK / 4) / kGemmThreads;
-    float4 v[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const int i = threadIdx.x + j * kGemmThreads;
         const int r = i / (kChunkK / 4), k = (i % (kChunkK / 4)) * 4;
         v[j] = __ldg(reinterpret_cast<const float4*>(X + (int64_t)(r0 + r) * ld + k0 + k));
     }
+}
+
+__device__ __forceinline__ void split_chunk(const float4 (&v)[kPer], char* dst)
+{
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const int i = threadIdx.x + j * kGemmThreads;
@@ -127,10 +132,10 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_split3_kernel(const Gemm
     if (J.a_off) J.A += J.a_off[J.img];
     if (J.c_off) J.C += J.c_off[J.img];
     const bool a_const = J.a_planes != nullptr, b_const = J.b_planes != nullptr;
-    // operands read from global memory and the row-major output move as 16-byte vectors;
-    // at most one operand comes pre-split
-    if ((!a_const && ((reinterpret_cast<uintptr_t>(J.A) & 15) || (J.lda & 3))) ||
-        (!b_const && ((reinterpret_cast<uintptr_t>(J.B) & 15) || (J.ldb & 3))) || (a_const && b_const) ||
+    // exactly one operand comes pre-split; the other and the row-major output move as
+    // 16-byte vectors
+    if (a_const == b_const || (!a_const && ((reinterpret_cast<uintptr_t>(J.A) & 15) || (J.lda & 3))) ||
+        (!b_const && ((reinterpret_cast<uintptr_t>(J.B) & 15) || (J.ldb & 3))) ||
         (!J.transpose_c && (reinterpret_cast<uintptr_t>(J.C) & 15))) {
         if (threadIdx.x == 0) atomicOr(status, kStatusBadOffset);
         return;
@@ -139,8 +144,12 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_split3_kernel(const Gemm
     const int tt = t - tile0[lo];
     const int m0 = (tt / tiles_n) * kTileM, n0 = (tt % tiles_n) * kTileN;
     const int chunks = J.K / kChunkK;
-    const char* ca = a_const ? J.a_planes + (size_t)(m0 / kTileM) * chunks * kTileBytes : nullptr;
-    const char* cb = b_const ? J.b_planes + (size_t)(n0 / kTileN) * chunks * kTileBytes : nullptr;
+    // the pre-split operand's tiles for this tile's rows, and the data operand
+    const char* cst = a_const ? J.a_planes + (size_t)(m0 / kTileM) * chunks * kTileBytes
+                              : J.b_planes + (size_t)(n0 / kTileN) * chunks * kTileBytes;
+    const float* X = a_const ? J.B : J.A;
+    const int64_t ldx = a_const ? J.ldb : J.lda;
+    const int rx = a_const ? n0 : m0;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
@@ -164,25 +173,27 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_split3_kernel(const Gemm
     int last_copy = -1, waited_copy = -1, last_commit = -1;   // thread 0's record of work in flight
     char* A = base;
     char* B = base + kTileBytes;
+    float4 v[kPer];
+    load_chunk(X, ldx, rx, 0, v);
     for (int ch = 0; ch < chunks; ++ch) {
         // the MMAs of chunk ch - 1 read the stage
         if (ch >= 1 && !mbar_wait(smem_u32(&bar_mma), (ch - 1) & 1)) {
             atomicOr(status, kStatusTimeout);
             s_abort = 1;
         }
-        if (threadIdx.x == 0 && (a_const || b_const)) {
-            bulk_g2s(smem_u32(a_const ? A : B), (a_const ? ca : cb) + (size_t)ch * kTileBytes, kTileBytes,
-                     smem_u32(&bar_ld));
+        if (threadIdx.x == 0) {
+            bulk_g2s(smem_u32(a_const ? A : B), cst + (size_t)ch * kTileBytes, kTileBytes, smem_u32(&bar_ld));
             last_copy = ch;
         }
-        if (!a_const) load_split(J.A, J.lda, m0, ch * kChunkK, A);
-        if (!b_const) load_split(J.B, J.ldb, n0, ch * kChunkK, B);
+        split_chunk(v, a_const ? B : A);
+        // the next chunk's data is in flight while the tensor core works on this one
+        if (ch + 1 < chunks) load_chunk(X, ldx, rx, (ch + 1) * kChunkK, v);
         // make the generic-proxy stores visible to the tensor core, then issue
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (s_abort) break;
         if (threadIdx.x == 0) {
-            const bool ok = !(a_const || b_const) || mbar_wait(smem_u32(&bar_ld), ch & 1);
+            const bool ok = mbar_wait(smem_u32(&bar_ld), ch & 1);
             if (!ok) {
                 atomicOr(status, kStatusTimeout);
                 s_abort = 1;
