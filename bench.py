@@ -613,7 +613,7 @@ def main():
                     help="corrector_train case: training pairs (batches of 4, one step each)")
     ap.add_argument("--case", default=None,
                     choices=["kernel4096", "corrector", "corrector_train", "corrector_small", "sisr_s2", "sisr_s4",
-                             "uneven2d", "images", "mci2d"],
+                             "uneven2d", "images", "mci2d", "hostlink"],
                     help="profiling case: the P=4096 size-class kernel alone on 3277 signals")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -707,6 +707,35 @@ def main():
         # every image workload: SISR x2/x4, x3 with M = 2 and 3, the blurred x3 set, uneven batch
         print(json.dumps({"case": args.case, **images_2d_section(mci, torch, dev, timed, args.steps)}),
               flush=True)
+        return
+    if args.case == "hostlink":
+        # the host link alone: copy-engine rates for the end-to-end step's bytes (input host to
+        # device, output device to host, both at once), page-locked host buffers
+        n_in, n_out = 309187584 // 4, 411725824 // 4
+        h_in = torch.empty(n_in, dtype=torch.float32).pin_memory()
+        h_out = torch.empty(n_out, dtype=torch.float32).pin_memory()
+        d_in = torch.empty(n_in, device=dev)
+        d_out = torch.empty(n_out, device=dev)
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def both():
+            with torch.cuda.stream(s1):
+                d_in.copy_(h_in, non_blocking=True)
+            with torch.cuda.stream(s2):
+                h_out.copy_(d_out, non_blocking=True)
+        out = {}
+        for name, fn, nbytes in (("h2d", lambda: d_in.copy_(h_in, non_blocking=True), 4 * n_in),
+                                 ("d2h", lambda: h_out.copy_(d_out, non_blocking=True), 4 * n_out),
+                                 ("both", both, 4 * (n_in + n_out))):
+            best = 1e9
+            for _ in range(max(3, args.steps)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            out[name] = {"bytes": nbytes, "ms": 1e3 * best, "gb_s": nbytes / best / 1e9}
+        print(json.dumps({"case": args.case, **out}), flush=True)
         return
     if args.case == "uneven2d":
         # profiling case: the uneven batch of 256 images (LR side in {128..1024}, s in {2,3,4})
