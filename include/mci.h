@@ -26,7 +26,10 @@
  *     index out of range, an image size the plan does not hold) make the
  *     kernels skip the affected signal or image and set a device status word
  *     that mci_plan_info reports.
- *   - No call allocates device memory except mci_plan (tables and workspace).
+ *   - No call allocates device memory except mci_plan (tables and workspace), and
+ *     mci_interp_1d_host when it stages buffers for a plan made with host_access 0 (its
+ *     first such call allocates the chunk buffers; a plan made with host_access 1 holds
+ *     them from mci_plan on).
  *   - The result of a real-sample reconstruction is the real part of the
  *     band-limited interpolant, as in the experiments of Section 5.1.
  */
@@ -293,10 +296,13 @@ mci_status mci_interp_1d_noalloc(mci_plan_t plan, const void* in, const int64_t*
  *   in, out      HOST, packed as in mci_interp_1d with NULL offsets; page-locked memory
  *                (cudaHostAlloc / registered) lets the copies run asynchronously.
  *   size_class   HOST array of batch class indices (NULL for a one-class plan).
- * The first call (and any call with larger chunks) allocates the chunk buffers (three
- * slots of input and output) and keeps them with the plan.  Work already queued on
+ * The chunk buffers (three slots of input and output) belong to the plan: with
+ * host_access 1 mci_plan allocates them, sized for any batch (a chunk holds at most
+ * max(16 MB, one signal) of input), so no call allocates; with host_access 0 the first
+ * call that stages allocates them and keeps them with the plan.  Work already queued on
  * `stream` runs first; the call returns when `out` holds the result (synchronous).
- * Errors: as mci_interp_1d; MCI_ERR_OOM when the chunk buffers cannot be allocated.
+ * Errors: as mci_interp_1d; MCI_ERR_OOM when the chunk buffers cannot be allocated
+ * (host_access 0 only; with host_access 1 mci_plan reports it).
  * There is no counterpart in the paper.
  */
 mci_status mci_interp_1d_host(mci_plan_t plan, const void* in, void* out, const int* size_class, int64_t batch,

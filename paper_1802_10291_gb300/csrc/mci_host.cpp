@@ -337,6 +337,9 @@ bool refuse_allocation()
     return c == 0;
 }
 
+// host-buffer path: input bytes per chunk of consecutive signals (one signal may exceed it)
+constexpr int64_t kChunkIn = (int64_t)16 << 20;
+
 cudaError_t dev_malloc(void** ptr, size_t bytes)
 {
     if (refuse_allocation()) return cudaErrorMemoryAllocation;
@@ -1316,6 +1319,29 @@ mci_status mci_plan(mci_plan_t* out, const mci_desc* desc, mci_stream_t stream)
         return cuda_status(e);
     }
     p->work_bytes = (int64_t)off;
+    // a plan that always stages host buffers (host_access 1) gets its chunk buffers now: a
+    // chunk holds at most max(kChunkIn, one signal) bytes of input, so at most that times the
+    // largest output/input ratio of the classes of output
+    if (e == cudaSuccess && d.host_access == 1 && B > 0) {
+        int64_t max_li = 0;
+        double ratio = 0.0;
+        for (const ClassDev& c : p->cdev) {
+            max_li = std::max(max_li, c.in_len * (int64_t)p->elem);
+            ratio = std::max(ratio, (double)c.out_len / (double)c.in_len);
+        }
+        const int64_t bin = std::max(kChunkIn, max_li);
+        const size_t need_in = align_up((size_t)bin, 256);
+        const size_t need_out = align_up((size_t)std::ceil((double)bin * ratio), 256);
+        e = dev_malloc((void**)&p->d_chunk, mci_plan_s::kSlots * (need_in + need_out));
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(s);
+            mci_destroy(p);
+            return cuda_status(e);
+        }
+        p->chunk_in_bytes = need_in;
+        p->chunk_out_bytes = need_out;
+        p->work_bytes += (int64_t)(mci_plan_s::kSlots * (need_in + need_out));
+    }
     char* w = (char*)p->d_work;
     p->d_status = (int*)(w + o_status);
     p->d_sorted = (int64_t*)(w + o_sorted);
@@ -1577,7 +1603,6 @@ mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int
     auto in_len = [&](int64_t b) { return p->cdev[n > 1 ? size_class[b] : 0].in_len; };
     auto out_len = [&](int64_t b) { return p->cdev[n > 1 ? size_class[b] : 0].out_len; };
     // chunks: consecutive signals up to kChunkIn bytes of input
-    const int64_t kChunkIn = (int64_t)16 << 20;
     std::vector<int64_t> first{0};
     std::vector<int64_t> ioff{0}, ooff{0};
     int64_t cin = 0, cout = 0, max_in = 0, max_out = 0;

@@ -118,9 +118,11 @@ def test_host_buffers_pipeline(cuda_device, pinned, access):
     plan.close()
 
 
-def test_refused_allocations_return_oom_and_free(cuda_device):
+@pytest.mark.parametrize("access", ["auto", "staged"])
+def test_refused_allocations_return_oom_and_free(cuda_device, access):
     """Every allocation of plan creation refused in turn (test hook): MCI_ERR_OOM, nothing
-    leaked on the device, and the first plan that gets all its memory works."""
+    leaked on the device, and the first plan that gets all its memory works.  A staged plan
+    also allocates its host-path chunk buffers at creation."""
     from paper_1802_10291_gb300 import mci as M
     systems = [("identity",), ("hilbert",), ("deriv", 1)]
     torch.cuda.synchronize()
@@ -130,7 +132,7 @@ def test_refused_allocations_return_oom_and_free(cuda_device):
         for k in range(32):
             M.mci_debug_fail_allocation(k)
             try:
-                plan = M.Plan(systems, [256, 512], [1024, 2048], max_batch=64)
+                plan = M.Plan(systems, [256, 512], [1024, 2048], max_batch=64, host_access=access)
             except M.MciError as e:
                 assert e.status == M.MCI_ERR_OOM, e.status
                 refused += 1
@@ -147,6 +149,32 @@ def test_refused_allocations_return_oom_and_free(cuda_device):
     plan.close()
     torch.cuda.synchronize()
     assert abs(torch.cuda.mem_get_info()[0] - free0) <= 64 << 20
+
+
+def test_staged_plan_host_calls_allocate_nothing(cuda_device):
+    """A plan made with host_access = staged holds its chunk buffers from creation: its
+    host-buffer calls, the first included, leave the device's free memory unchanged."""
+    systems = [("identity",), ("hilbert",), ("deriv", 1)]
+    PS = [256, 512, 1024]
+    plan = mci.Plan(systems, PS, [4 * p for p in PS], max_batch=4096, host_access="staged")
+    rng = np.random.default_rng(7)
+    cls = rng.integers(0, 3, 3000).astype(np.int32)
+    P = np.array(PS)[cls]
+    h_in = torch.tensor(rng.standard_normal(int(3 * P.sum())), dtype=torch.float32).pin_memory()
+    h_out = torch.empty(int(4 * P.sum()), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        mci.mci_interp_1d_host(plan.handle, h_in, h_out, cls, len(cls))
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= 4 << 20
+    assert plan.info()["device_status"] == 0 and torch.isfinite(h_out).all()
+    # the same batch through device buffers gives the same samples
+    d_out = torch.empty_like(h_out, device="cuda")
+    mci.mci_interp_1d(plan.handle, h_in.cuda(), None, d_out, None, torch.tensor(cls, device="cuda"), len(cls))
+    torch.cuda.synchronize()
+    assert torch.equal(d_out.cpu(), h_out)
+    plan.close()
 
 
 def test_autotune_cache_reused_and_saved(cuda_device, tmp_path):
