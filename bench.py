@@ -44,7 +44,7 @@ CPU_PER_CLASS = 100
 # DRAM bytes (read + write) of one launch of the roofline kernel (the persistent launch that
 # serves the whole batched step), from one ncu capture of that launch on this workload.
 # None whenever the kernel has changed since the capture.
-ROOFLINE_TRAFFIC_PER_STEP = 310033664 + 356902144
+ROOFLINE_TRAFFIC_PER_STEP = 310034944 + 357062144
 # the same for the P = 4096 class kernel timed alone (3201 signals), per signal
 CLASS4096_TRAFFIC_PER_SIGNAL = (157665024 + 153586688) / 3201
 
