@@ -22,6 +22,8 @@ Functions and the passage each follows:
   Section 3 directly (minimum-norm least squares).
 * :func:`fd_channels` -- the three-point centred differences of Section 5.2.
 * :func:`upsample_2d` -- rows then columns, Section 5.2.
+* :func:`upsample_2d_mirror` -- the same on the half-sample-symmetric extension
+  of the image (mirror boundaries instead of the periodic wrap of Section 2).
 * :func:`blur_factor`, :func:`blur_systems` -- the blur-aware channel model that
   Section 5.2 lists as an open extension: every channel is the system response
   blurred by a periodic Gaussian on the output grid, so each b_m(n) carries the
@@ -377,6 +379,18 @@ def upsample_2d(img, scale, systems, policy="pinv", nthreads=0, blur=None):
     cols = mci_direct(model(h, scale * h), fd_channels(rows.T, systems), scale * h,
                       policy=policy, nthreads=nthreads)[:, 0, :]       # sw x sh
     return cols.T
+
+
+def upsample_2d_mirror(img, scale, systems, policy="pinv", nthreads=0):
+    """Separable 2-D MCI with mirror (half-sample-symmetric) image boundaries in place of the
+    periodic wrap that the method assumes (Section 2: 2 pi-periodic signals): the h x w image
+    is reflected about its edges to 2h x 2w (sample P + n repeats sample P - 1 - n), that
+    extension is interpolated as a periodic image by :func:`upsample_2d`, and the s h x s w
+    block over the original image is kept."""
+    img = np.asarray(img, np.float64)
+    h, w = img.shape
+    ext = np.pad(img, ((0, h), (0, w)), mode="symmetric")
+    return upsample_2d(ext, scale, systems, policy, nthreads)[: scale * h, : scale * w]
 
 
 def error_bound(coeff_fn, systems, P, N1=None, n_max=None, policy="pinv", rtol=1e-13):
