@@ -256,6 +256,30 @@ mci_status mci_upsample_2d(mci_plan_t plan, const float* lr, const int64_t* lr_o
                            int64_t n_img, mci_stream_t stream);
 
 /*
+ * mci_upsample_2d_mirror -- mci_upsample_2d with mirror image boundaries.  The method
+ * interpolates periodic signals (Section 2), so mci_upsample_2d treats an image as one period
+ * and its opposite edges meet; here each h x w image is first reflected about its edges to
+ * 2h x 2w (row or column P + n repeats P - 1 - n), that extension is interpolated as a
+ * periodic image, and the (s h) x (s w) block over the original image is written to hr.  The
+ * paper leaves the image boundary open; mirror extension is the usual remedy for the ringing
+ * of the periodic wrap.
+ *   lr       device float, packed h_i x w_i images
+ *   h, w     HOST int arrays; the plan must hold the classes (2 w, 2 s w) and (2 h, 2 s h),
+ *            max_images >= n_img and max_intermediate >= sum 4 s_i h_i w_i
+ *   scale    HOST int array of scale factors
+ *   hr       device float, packed (s h) x (s w) images
+ *   n_img    0 .. 256 (MCI_ERR_UNSUPPORTED_SIZE above)
+ *   ext_lr   device float scratch of sum 4 h_i w_i elements (the extended images)
+ *   ext_hr   device float scratch of sum 4 s_i^2 h_i w_i elements (their interpolation)
+ * The caller owns both scratch buffers (the call allocates nothing); they, the plan's
+ * workspace and hr are written on `stream`, so calls on one plan or one scratch must not
+ * overlap.  Errors: as mci_upsample_2d.
+ */
+mci_status mci_upsample_2d_mirror(mci_plan_t plan, const float* lr, const int* h, const int* w,
+                                  const int* scale, float* hr, int64_t n_img, float* ext_lr,
+                                  float* ext_hr, mci_stream_t stream);
+
+/*
  * mci_interp_1d_noalloc -- the same computation as mci_interp_1d, with the
  * same arguments except that size_class must be in DEVICE (or managed)
  * memory, for callers that cannot allocate device memory at the time

@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-rdc=true", "-Xcompiler", "-fPI
 # host plan code is plain C++ (g++); kernels and the device-side scheduler are CUDA with
 # relocatable device code, because the scheduler launches the size-class kernels.
 HOST_UNITS = ["mci_host.cpp", "mci2d_host.cpp"]
-CUDA_UNITS = ["mci_fast.cu", "mci_sched.cu", "mci_noalloc.cu", "mci_gemm.cu", "mci_error.cu", "mci_corrector.cu", "mci2d.cu", "k_lookup.cu", "k_a.cu", "k_b.cu", "k_c.cu", "k_d.cu", "k_e.cu"]
+CUDA_UNITS = ["mci_fast.cu", "mci_mirror.cu", "mci_sched.cu", "mci_noalloc.cu", "mci_gemm.cu", "mci_error.cu", "mci_corrector.cu", "mci2d.cu", "k_lookup.cu", "k_a.cu", "k_b.cu", "k_c.cu", "k_d.cu", "k_e.cu"]
 UNITS = HOST_UNITS + CUDA_UNITS
 
 

@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
         lib.mci_interp_1d.restype = ctypes.c_int
         lib.mci_interp_1d_host.argtypes = [vp, vp, vp, vp, i64, vp]
         lib.mci_interp_1d_host.restype = ctypes.c_int
+        lib.mci_upsample_2d_mirror.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp]
+        lib.mci_upsample_2d_mirror.restype = ctypes.c_int
         lib.mci_averaged_error.argtypes = [vp, ctypes.c_int, vp, i64, i64, vp, vp, vp]
         lib.mci_averaged_error.restype = ctypes.c_int
         lib.mci_interp_1d_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
@@ -279,6 +281,14 @@ def mci_upsample_2d(plan: int, lr, lr_off, h, w, scale, hr, hr_off, n_img: int, 
     _check(load().mci_upsample_2d(plan, _ptr(lr), _ptr(lr_off), _ptr(h), _ptr(w), _ptr(scale),
                                   _ptr(hr), _ptr(hr_off), int(n_img), _stream(stream)),
            "mci_upsample_2d")
+
+
+def mci_upsample_2d_mirror(plan: int, lr, h, w, scale, hr, n_img: int, ext_lr, ext_hr, stream=None):
+    """mci_upsample_2d on the mirror extension of each image (h, w, scale: host int32 arrays;
+    ext_lr, ext_hr: device float scratch of sum 4 h w and sum 4 s^2 h w elements)."""
+    _check(load().mci_upsample_2d_mirror(plan, _ptr(lr), _ptr(h), _ptr(w), _ptr(scale), _ptr(hr),
+                                         int(n_img), _ptr(ext_lr), _ptr(ext_hr), _stream(stream)),
+           "mci_upsample_2d_mirror")
 
 
 def mci_plan_info(plan: int) -> dict:

@@ -11,7 +11,8 @@ from paper_1802_10291_gb300 import mci
 
 def test_exports_every_declared_symbol(mci_lib):
     declared = mci.header_functions()
-    assert set(declared) == {"mci_plan", "mci_interp_1d", "mci_upsample_2d", "mci_plan_info", "mci_averaged_error", "mci_interp_1d_host",
+    assert set(declared) == {"mci_plan", "mci_interp_1d", "mci_upsample_2d", "mci_upsample_2d_mirror", "mci_plan_info",
+                             "mci_averaged_error", "mci_interp_1d_host",
                              "mci_destroy", "mci_error_string", "mci_interp_1d_noalloc",
                              "mci_corrector_num_params", "mci_corrector_create", "mci_corrector_forward",
                              "mci_corrector_loss_grad", "mci_corrector_train_step",
