@@ -356,10 +356,13 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
                         v[S + u] = y[u][e].y;
                     }
                     if constexpr (S % 2 == 0 && N >= 256) {
-                        // the rotation (4 g or 8 g words) keeps the 2S-word chunks 16-byte aligned
+                        // the rotation (4 g or 8 g words) keeps the 2S-word chunks 16-byte aligned;
+                        // with s = 4 the two chunks of lanes with bit 2 of l set trade places, so
+                        // a quarter warp's eight 16-byte stores hit eight different bank groups
+                        // (row x sits at word x ^ ((x >> 3) & 4))
 #pragma unroll
                         for (int k = 0; k < S / 2; ++k) {
-                            int pos = 2 * S * l + 4 * k + rot;
+                            int pos = 2 * S * l + 4 * (S == 4 ? k ^ ((l >> 2) & 1) : k) + rot;
                             if (pos >= T) pos -= T;
                             *reinterpret_cast<float4*>(oc + pos) =
                                 make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
@@ -381,13 +384,15 @@ __device__ __forceinline__ void fast_tile(const FastTile& ft, unsigned char* sme
                 const float* srcc = reinterpret_cast<const float*>(reinterpret_cast<C*>(smem_raw) + gs * QM * N);
                 float* dst = ft.out + ft.s_out[0] + gs + (int64_t)x0 * ft.ld;
                 const int64_t step = (int64_t)(256 / G) * ft.ld;
-                int pos = x0 + col_rot<N>(gs);   // < 256 / G + 32 <= T
+                const int rg = col_rot<N>(gs);
+                int x = x0;
 #pragma unroll 8
                 for (int k = 0; k < T / (256 / G); ++k) {
+                    int pos = (S == 4 && N >= 256 ? x ^ ((x >> 3) & 4) : x) + rg;   // < T + 32
+                    if (pos >= T) pos -= T;
                     __stcs(dst, srcc[pos]);
                     dst += step;
-                    pos += 256 / G;
-                    if (pos >= T) pos -= T;
+                    x += 256 / G;
                 }
             }
             return;
