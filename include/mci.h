@@ -161,9 +161,12 @@ typedef struct {
     int host_access;         /* mci_interp_1d_host only.  0: when both buffers are page-locked
                                 and mapped into the device address space (cudaHostAlloc /
                                 cudaHostRegister, as reported by cudaPointerGetAttributes), the
-                                kernels read the input and write the output in host memory
-                                directly over the host link, without staging copies; other
-                                buffers are staged.  1: always stage through device chunks.  */
+                                kernels can read the input and write the output in host memory
+                                directly over the host link, without staging copies; the first
+                                three such calls on the plan time that route and the staged
+                                one (the second call stages untimed) and the plan keeps the
+                                faster per byte (mci_plan_stats.host_route); other buffers are
+                                staged.  1: always stage through device chunks.  */
 } mci_desc;
 
 typedef struct {
@@ -184,6 +187,8 @@ typedef struct {
                                 batches when every class is fused (0: one launch per class) */
     unsigned fused3_mask;    /* bit c: the image columns of size class c (N = 3 N') run on
                                 the fused factor-3 column kernel                            */
+    int host_route;          /* mci_interp_1d_host with device-mapped buffers (host_access
+                                0): 0 still measuring, 1 zero copy, 2 staged                */
 } mci_plan_stats;
 
 /*

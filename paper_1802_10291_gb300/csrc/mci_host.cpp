@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstdlib>
@@ -320,6 +321,11 @@ struct mci_plan_s {
     static constexpr int kSlots = 3;
     void* d_chunk = nullptr;             // kSlots x (chunk input | chunk output)
     size_t chunk_in_bytes = 0, chunk_out_bytes = 0;
+    // host_access 0 with device-mapped buffers: 0 times the zero-copy route next, 1 runs the
+    // staged route untimed (it may allocate), 2 times it, 3 decided (host_zero_copy)
+    int host_trial = 0;
+    bool host_zero_copy = true;
+    double host_rate[2] = {0.0, 0.0};    // bytes per second: zero copy, staged
     cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev_in[kSlots] = {}, ev_comp[kSlots] = {}, ev_free[kSlots] = {};
 };
@@ -1563,6 +1569,7 @@ mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)
         if (p->cdev[c].fast) st->fused_mask |= 1u << c;
     for (size_t c = 0; c < p->cdev.size(); ++c)
         if (p->cdev[c].fast3) st->fused3_mask |= 1u << c;
+    st->host_route = p->host_trial < 3 ? 0 : (p->host_zero_copy ? 1 : 2);
     st->persistent_ctas = p->persist ? p->persist_ctas : 0;
     cudaError_t e = cudaStreamSynchronize(p->last_stream);
     int status = 0;
@@ -1576,30 +1583,12 @@ mci_status mci_plan_info(mci_plan_t p, mci_plan_stats* st)
 // input each); chunk c uses slot c mod 3 of device buffers and moves through three streams:
 // copy in -> compute (mci_interp_1d, size classes grouped on the host) -> copy out, so the
 // two copy directions and the compute of neighbouring chunks overlap.
-mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int* size_class, int64_t batch,
-                              mci_stream_t stream)
+// The staged host-buffer route: chunks of consecutive signals through the copy-in, compute
+// and copy-out streams.
+static mci_status interp_1d_host_staged(mci_plan_t p, const void* in, void* out, const int* size_class,
+                                        int64_t batch, mci_stream_t stream)
 {
-    if (!p || batch < 0 || batch > p->desc.max_batch) return MCI_ERR_INVALID_ARG;
-    if (batch == 0) return MCI_OK;
     const int n = (int)p->cls.size();
-    if (!in || !out || (n > 1 && !size_class)) return MCI_ERR_INVALID_ARG;
-    for (int64_t b = 0; b < batch && n > 1; ++b)
-        if (size_class[b] < 0 || size_class[b] >= n) return MCI_ERR_INVALID_ARG;
-    if (p->desc.host_access == 0) {
-        // page-locked, device-mapped buffers on both sides: the kernels read and write them in
-        // place over the host link (the runtime's device addresses of the two buffers)
-        cudaPointerAttributes ai{}, ao{};
-        const bool qi = cudaPointerGetAttributes(&ai, in) == cudaSuccess;
-        const bool qo = qi && cudaPointerGetAttributes(&ao, out) == cudaSuccess;
-        if (!qo) cudaGetLastError();
-        if (qo && ai.type == cudaMemoryTypeHost && ao.type == cudaMemoryTypeHost && ai.devicePointer &&
-            ao.devicePointer) {
-            const mci_status st = mci_interp_1d(p, ai.devicePointer, nullptr, ao.devicePointer, nullptr,
-                                                size_class, batch, stream);
-            if (st != MCI_OK) return st;
-            return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? MCI_OK : MCI_ERR_CUDA;
-        }
-    }
     auto in_len = [&](int64_t b) { return p->cdev[n > 1 ? size_class[b] : 0].in_len; };
     auto out_len = [&](int64_t b) { return p->cdev[n > 1 ? size_class[b] : 0].out_len; };
     // chunks: consecutive signals up to kChunkIn bytes of input
@@ -1679,6 +1668,56 @@ mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int
     if (e == cudaSuccess) e = cudaStreamSynchronize(s_out);
     p->last_stream = s;
     return cuda_status(e);
+}
+
+mci_status mci_interp_1d_host(mci_plan_t p, const void* in, void* out, const int* size_class, int64_t batch,
+                              mci_stream_t stream)
+{
+    if (!p || batch < 0 || batch > p->desc.max_batch) return MCI_ERR_INVALID_ARG;
+    if (batch == 0) return MCI_OK;
+    const int n = (int)p->cls.size();
+    if (!in || !out || (n > 1 && !size_class)) return MCI_ERR_INVALID_ARG;
+    for (int64_t b = 0; b < batch && n > 1; ++b)
+        if (size_class[b] < 0 || size_class[b] >= n) return MCI_ERR_INVALID_ARG;
+    if (p->desc.host_access == 0) {
+        // page-locked, device-mapped buffers on both sides: the kernels can read and write them
+        // in place over the host link (the runtime's device addresses of the two buffers).
+        // Which of that and the staged route is faster depends on the machine (where the pages
+        // sit relative to the GPU): the first calls time both, per byte, and the plan keeps
+        // the faster
+        cudaPointerAttributes ai{}, ao{};
+        const bool qi = cudaPointerGetAttributes(&ai, in) == cudaSuccess;
+        const bool qo = qi && cudaPointerGetAttributes(&ao, out) == cudaSuccess;
+        if (!qo) cudaGetLastError();
+        if (qo && ai.type == cudaMemoryTypeHost && ao.type == cudaMemoryTypeHost && ai.devicePointer &&
+            ao.devicePointer) {
+            double bytes = 0.0;
+            for (int64_t b = 0; b < batch; ++b) {
+                const ClassDev& c = p->cdev[n > 1 ? size_class[b] : 0];
+                bytes += (double)(c.in_len + c.out_len) * p->elem;
+            }
+            const int trial = p->host_trial;
+            const auto t0 = std::chrono::steady_clock::now();
+            mci_status st;
+            if (trial == 3 ? p->host_zero_copy : trial == 0) {
+                st = mci_interp_1d(p, ai.devicePointer, nullptr, ao.devicePointer, nullptr, size_class, batch, stream);
+                if (st == MCI_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) st = MCI_ERR_CUDA;
+            } else {
+                st = interp_1d_host_staged(p, in, out, size_class, batch, stream);
+            }
+            const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (st == MCI_OK && trial < 3) {
+                if (trial == 0) p->host_rate[0] = bytes / dt;
+                if (trial == 2) {
+                    p->host_rate[1] = bytes / dt;
+                    p->host_zero_copy = p->host_rate[0] >= p->host_rate[1];
+                }
+                p->host_trial = trial + 1;
+            }
+            return st;
+        }
+    }
+    return interp_1d_host_staged(p, in, out, size_class, batch, stream);
 }
 
 mci_status mci_interp_1d_noalloc(mci_plan_t p, const void* in, const int64_t* in_off, void* out,

@@ -72,7 +72,7 @@ class mci_plan_stats(ctypes.Structure):
                 ("threads_per_cta", ctypes.c_int), ("smem_bytes", ctypes.c_int),
                 ("table_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("fused_mask", ctypes.c_uint), ("persistent_ctas", ctypes.c_int),
-                ("fused3_mask", ctypes.c_uint)]
+                ("fused3_mask", ctypes.c_uint), ("host_route", ctypes.c_int)]
 
 
 _lib = None
@@ -299,7 +299,7 @@ def mci_plan_info(plan: int) -> dict:
             "threads_per_cta": st.threads_per_cta, "smem_bytes": st.smem_bytes,
             "table_bytes": st.table_bytes, "workspace_bytes": st.workspace_bytes,
             "fused_mask": st.fused_mask, "persistent_ctas": st.persistent_ctas,
-            "fused3_mask": st.fused3_mask}
+            "fused3_mask": st.fused3_mask, "host_route": st.host_route}
 
 
 def mci_destroy(plan: int):

@@ -151,6 +151,33 @@ def test_refused_allocations_return_oom_and_free(cuda_device, access):
     assert abs(torch.cuda.mem_get_info()[0] - free0) <= 64 << 20
 
 
+def test_auto_host_route_settles_and_agrees(cuda_device):
+    """host_access auto with device-mapped buffers: the first three calls time the zero-copy
+    and the staged routes, then the plan keeps one; every call's output equals the
+    device-buffer call bit for bit."""
+    systems = [("identity",), ("hilbert",), ("deriv", 1)]
+    PS = [256, 512, 1024]
+    plan = mci.Plan(systems, PS, [4 * p for p in PS], max_batch=8192)
+    rng = np.random.default_rng(11)
+    cls = rng.integers(0, 3, 6000).astype(np.int32)   # several 16 MB chunks when staged
+    P = np.array(PS)[cls]
+    h_in = torch.tensor(rng.standard_normal(int(3 * P.sum())), dtype=torch.float32).pin_memory()
+    h_out = torch.empty(int(4 * P.sum()), dtype=torch.float32).pin_memory()
+    d_out = torch.empty_like(h_out, device="cuda")
+    mci.mci_interp_1d(plan.handle, h_in.cuda(), None, d_out, None, torch.tensor(cls, device="cuda"), len(cls))
+    torch.cuda.synchronize()
+    ref = d_out.cpu()
+    routes = []
+    for _ in range(5):
+        h_out.fill_(float("nan"))
+        mci.mci_interp_1d_host(plan.handle, h_in, h_out, cls, len(cls))
+        assert torch.equal(h_out, ref)
+        routes.append(plan.info()["host_route"])
+    assert routes[:2] == [0, 0] and routes[2] in (1, 2) and len(set(routes[2:])) == 1, routes
+    assert plan.info()["device_status"] == 0
+    plan.close()
+
+
 def test_staged_plan_host_calls_allocate_nothing(cuda_device):
     """A plan made with host_access = staged holds its chunk buffers from creation: its
     host-buffer calls, the first included, leave the device's free memory unchanged."""
