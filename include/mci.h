@@ -278,7 +278,8 @@ mci_status mci_upsample_2d(mci_plan_t plan, const float* lr, const int64_t* lr_o
  *   ext_hr   device float scratch of sum 4 s_i^2 h_i w_i elements (their interpolation)
  * The caller owns both scratch buffers (the call allocates nothing); they, the plan's
  * workspace and hr are written on `stream`, so calls on one plan or one scratch must not
- * overlap.  Errors: as mci_upsample_2d.
+ * overlap.  Errors: as mci_upsample_2d; MCI_ERR_INVALID_ARG when lr, hr or a scratch
+ * buffer is not device (or managed) memory.
  */
 mci_status mci_upsample_2d_mirror(mci_plan_t plan, const float* lr, const int* h, const int* w,
                                   const int* scale, float* hr, int64_t n_img, float* ext_lr,

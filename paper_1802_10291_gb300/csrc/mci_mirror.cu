@@ -75,6 +75,15 @@ extern "C" mci_status mci_upsample_2d_mirror(mci_plan_t plan, const float* lr, c
     if (n_img == 0) return MCI_OK;
     if (n_img > kMirrorMaxImages) return MCI_ERR_UNSUPPORTED_SIZE;
     if (!lr || !h || !w || !scale || !hr || !ext_lr || !ext_hr) return MCI_ERR_INVALID_ARG;
+    // the kernels below read and write these four directly: device (or managed) memory only
+    for (const void* ptr : {(const void*)lr, (const void*)hr, (const void*)ext_lr, (const void*)ext_hr}) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return MCI_ERR_INVALID_ARG;
+        }
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return MCI_ERR_INVALID_ARG;
+    }
     MirrorDims d{};
     d.n = (int)n_img;
     std::vector<int> h2((size_t)n_img), w2((size_t)n_img);

@@ -93,4 +93,8 @@ def test_mirror_rejects_bad_arguments(cuda_device):
     with pytest.raises(mci.MciError) as e:   # no scratch
         mci.mci_upsample_2d_mirror(plan.handle, lr, one * 16, one * 16, one * 2, hr, 1, None, ext)
     assert e.value.status == mci.MCI_ERR_INVALID_ARG
+    with pytest.raises(mci.MciError) as e:   # scratch in host memory: refused before any kernel
+        host_ext = torch.zeros(4096)
+        mci.mci_upsample_2d_mirror(plan.handle, lr, one * 16, one * 16, one * 2, hr, 1, host_ext, ext)
+    assert e.value.status == mci.MCI_ERR_INVALID_ARG
     plan.close()
