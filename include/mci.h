@@ -244,8 +244,10 @@ mci_status mci_interp_1d(mci_plan_t plan, const void* in, const int64_t* in_off,
  *   lr_off   device int64 element offsets, or NULL (packed)
  *   h, w     int arrays of image heights and widths
  *   scale    int array of scale factors s_i >= 1.  h, w and scale all in DEVICE
- *            memory: the batch is grouped on the device and launched from there
- *            (stream-capturable; bad sizes set device_status bits).  All in HOST
+ *            memory: the batch is grouped on the device; the size classes are launched
+ *            from the host with grids bounded by the plan's limits (extra CTAs exit at
+ *            once) when those bounds are small, else from the device
+ *            (stream-capturable either way; bad sizes set device_status bits).  All in HOST
  *            memory: grouping on the host, one upload from pinned staging,
  *            exact-grid launches per class from the host -- the faster path;
  *            an image size the plan does not hold returns

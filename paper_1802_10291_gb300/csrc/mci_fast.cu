@@ -458,6 +458,8 @@ __global__ void __launch_bounds__(256, 2) mci_fast_kernel(const KArgs a)
     __shared__ int64_t s_in[kMaxTile];
     __shared__ int64_t s_out[kMaxTile];
     __shared__ int s_cnt;
+    // image rows: a grid may exceed the class's tile count (bounded host launches)
+    if (a.mode == kModeRows && (int)blockIdx.x >= a.sched2->row_count[a.cls]) return;
     const int list0 = a.mode == kModeRows ? a.sched2->row_start[a.cls] : 0;
     const int cnt = tile_signal_offsets(a, 2048 / N, blockIdx.x, list0, s_in, s_out, &s_cnt);
     const C* W = static_cast<const C*>(a.W);
@@ -475,6 +477,7 @@ __global__ void __launch_bounds__(256, 2) mci_fast_cols_kernel(const KArgs a)
     __shared__ int64_t s_in[kMaxTile];
     __shared__ int64_t s_out[kMaxTile];
     constexpr int G = 2048 / N;
+    if ((int)blockIdx.x >= a.sched2->col_count[a.cls]) return;   // bounded host launches
     const int2 it = a.items[a.sched2->col_start[a.cls] + blockIdx.x];
     const int i = it.x;
     const int64_t ld = (int64_t)a.scale[i] * a.w[i];   // intermediate and HR row pitch
@@ -612,6 +615,7 @@ __global__ void __launch_bounds__(256, 2) mci_fast3_cols_kernel(const KArgs a)
     constexpr int N = 3 * NQ, P = 2 * N, TPS = NQ / 8, G = 2048 / NQ, L = fast_passes(NQ);
     constexpr int RPI = 256 / G;   // rows per staging step
     static_assert(NQ >= 64 && NQ <= 256 && (NQ & (NQ - 1)) == 0 && (P * G) % 256 == 0, "factor-3 column class");
+    if ((int)blockIdx.x >= a.sched2->col_count[a.cls]) return;   // bounded host launches
     const int2 item = a.items[a.sched2->col_start[a.cls] + blockIdx.x];
     const int img = item.x;
     const int64_t ld = (int64_t)a.scale[img] * a.w[img];   // intermediate and HR row pitch

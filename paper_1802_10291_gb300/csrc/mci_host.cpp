@@ -343,6 +343,10 @@ bool refuse_allocation()
     return c == 0;
 }
 
+// device-grouped 2-D batches: classes are launched from the host with bounded grids when the
+// bounds of all classes add up to at most this many CTAs
+constexpr int64_t kBoundedCtas = 16384;
+
 // host-buffer path: input bytes per chunk of consecutive signals (one signal may exceed it)
 constexpr int64_t kChunkIn = (int64_t)16 << 20;
 
@@ -1511,10 +1515,47 @@ mci_status mci_upsample_2d(mci_plan_t p, const float* lr, const int64_t* lr_off,
     }
     if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
         return upsample_2d_host_grouped(p, rows, cols, h, w, scale, !lr_off, !hr_off, n_img, s);
-    const int e = launch_sched_2d(n_img, (int)p->cls.size(), p->d_launch, p->desc.max_intermediate,
-                                  p->max_items, p->d_inter_off, lr_off ? nullptr : p->d_lr_pref,
-                                  hr_off ? nullptr : p->d_hr_pref, p->d_row_cls, p->d_col_cls,
-                                  p->d_items, p->d_sched2, rows, cols, s);
+    // Device grouping.  Each class's tile count is known only on the device, but bounded by
+    // the plan: rows: n_img ceil(P_max / G) and max_intermediate / (P G) + n_img; columns:
+    // n_img ceil(T_max / Gc) and max_intermediate / (P Gc) + n_img.  When the bounds add up
+    // to few CTAs, every class is launched from the host with its bound as the grid (the
+    // CTAs beyond the count leave at once): no launches from the device, whose latency
+    // dominates small batches.  Otherwise the scheduler launches the classes itself.
+    const int n = (int)p->cls.size();
+    int Pmax = 0, Tmax = 0;
+    for (const HostClass& hc : p->cls) {
+        Pmax = std::max(Pmax, hc.P);
+        Tmax = std::max(Tmax, hc.T);
+    }
+    const int64_t X = p->desc.max_intermediate;
+    std::vector<int64_t> brow(n), bcol(n);
+    int64_t total = 0;
+    for (int c = 0; c < n; ++c) {
+        const ClassDev& cd = p->cdev[c];
+        brow[c] = std::min<int64_t>(n_img * ((Pmax + cd.G - 1) / cd.G), X / ((int64_t)cd.P * cd.G) + n_img);
+        bcol[c] = std::min<int64_t>(n_img * ((Tmax + cd.Gc - 1) / cd.Gc), X / ((int64_t)cd.P * cd.Gc) + n_img);
+        total += brow[c] + bcol[c];
+    }
+    const bool host_launch = total <= kBoundedCtas;
+    int e = launch_sched_2d(n_img, n, p->d_launch, X, p->max_items, p->d_inter_off,
+                            lr_off ? nullptr : p->d_lr_pref, hr_off ? nullptr : p->d_hr_pref, p->d_row_cls,
+                            p->d_col_cls, p->d_items, p->d_sched2, rows, cols, s, host_launch ? 0 : 1);
+    for (int pass = 0; pass < 2 && host_launch && e == 0; ++pass) {
+        const bool cpass = pass == 1;
+        for (int c = 0; c < n && e == 0; ++c) {
+            const int64_t grid = cpass ? bcol[c] : brow[c];
+            const void* k = cpass ? p->kern_cols[c] : p->kern[c];
+            if (grid <= 0 || !k) continue;
+            KArgs ac = cpass ? cols : rows;
+            ac.c = p->cdev[c];
+            ac.cls = c;
+            ac.W = p->launch[c].W;
+            ac.mode = cpass ? kModeCols : kModeRows;
+            void* args[] = {&ac};
+            e = (int)cudaLaunchKernel(k, dim3((unsigned)grid), dim3(kThreads), args,
+                                      (size_t)(cpass ? p->csmem_cols[c] : p->csmem[c]), s);
+        }
+    }
     return e ? MCI_ERR_CUDA : MCI_OK;
 }
 

@@ -263,7 +263,7 @@ int launch_sched_1d(const int* size_class, int64_t batch, int n_classes, const C
 int launch_sched_2d(int64_t n_img, int n_classes, const ClassLaunch* cl, int64_t max_inter,
                     int64_t max_items, int64_t* inter_off, int64_t* lr_pref, int64_t* hr_pref,
                     int* row_cls, int* col_cls, int2* items, Sched2D* st, const KArgs& rows_tmpl,
-                    const KArgs& cols_tmpl, void* stream);
+                    const KArgs& cols_tmpl, void* stream, int child);
 
 // Tensor-core GEMM (mci_gemm.cu): tile0 is the tile prefix over jobs (n_jobs + 1).
 int launch_gemm(const GemmJob* jobs, const int* tile0, int n_jobs, int n_tiles, int* status,

@@ -104,8 +104,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2) mci_kernel(c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
     int list0 = 0;
-    if (a.mode == kModeRows) list0 = a.sched2->row_start[a.cls];
-    else if (a.mode == kModeCols) list0 = a.sched2->col_start[a.cls];
+    // image passes: a grid may exceed the class's tile count (host launches sized by a bound
+    // for device-grouped batches); the extra CTAs leave at once
+    if (a.mode == kModeRows) {
+        if ((int)blockIdx.x >= a.sched2->row_count[a.cls]) return;
+        list0 = a.sched2->row_start[a.cls];
+    } else if (a.mode == kModeCols) {
+        if ((int)blockIdx.x >= a.sched2->col_count[a.cls]) return;
+        list0 = a.sched2->col_start[a.cls];
+    }
     mci_tile_item<R, N, COLS>(a, blockIdx.x, list0, sm);
 }
 

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kSchedThreads)
 sched_2d_kernel(int64_t n_img, int n_classes, const ClassLaunch* __restrict__ cl,
                 int64_t max_inter, int64_t max_items, int64_t* inter_off, int64_t* lr_pref,
                 int64_t* hr_pref, int* row_cls, int* col_cls, int2* items, Sched2D* st,
-                KArgs tmpl)
+                KArgs tmpl, int child)
 {
     __shared__ int rcnt[MCI_MAX_SIZES], ccnt[MCI_MAX_SIZES];
     __shared__ int rcur[MCI_MAX_SIZES], ccur[MCI_MAX_SIZES];
@@ -256,7 +256,7 @@ sched_2d_kernel(int64_t n_img, int n_classes, const ClassLaunch* __restrict__ cl
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0 && ok_all) {
+    if (threadIdx.x == 0 && ok_all && child) {
         for (int c = 0; c < n_classes; ++c) {
             if (rcnt[c] == 0) continue;
             KArgs a = tmpl;
@@ -288,14 +288,14 @@ __global__ void dispatch_cols_kernel(int n_classes, const ClassLaunch* __restric
 int launch_sched_2d(int64_t n_img, int n_classes, const ClassLaunch* cl, int64_t max_inter,
                     int64_t max_items, int64_t* inter_off, int64_t* lr_pref, int64_t* hr_pref,
                     int* row_cls, int* col_cls, int2* items, Sched2D* st, const KArgs& rows_tmpl,
-                    const KArgs& cols_tmpl, void* stream)
+                    const KArgs& cols_tmpl, void* stream, int child)
 {
     cudaStream_t s = (cudaStream_t)stream;
     sched_2d_kernel<<<1, kSchedThreads, 0, s>>>(n_img, n_classes, cl, max_inter, max_items,
                                                  inter_off, lr_pref, hr_pref, row_cls, col_cls,
-                                                 items, st, rows_tmpl);
+                                                 items, st, rows_tmpl, child);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return (int)e;
+    if (e != cudaSuccess || !child) return (int)e;
     dispatch_cols_kernel<<<1, 32, 0, s>>>(n_classes, cl, st, cols_tmpl);
     return (int)cudaGetLastError();
 }
