@@ -165,8 +165,10 @@ typedef struct {
                                 directly over the host link, without staging copies; the first
                                 three such calls on the plan time that route and the staged
                                 one (the second call stages untimed) and the plan keeps the
-                                faster per byte (mci_plan_stats.host_route); other buffers are
-                                staged.  1: always stage through device chunks.  */
+                                faster per byte (mci_plan_stats.host_route; the plan keeps
+                                that state, so one plan's host calls must not run from several
+                                host threads at once); other buffers are staged.
+                                1: always stage through device chunks.  */
 } mci_desc;
 
 typedef struct {
